@@ -1,0 +1,173 @@
+"""Python access to the CPU oracle (oracle/chem_oracle.cpp).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU
+baseline leg use this module to compute reference results.  Nothing on the product path
+imports it.  The oracle shares no code with the CUDA library; both read the same mechanism
+file, each with its own parser.
+
+Parity status of each function (what pins it, see tests/test_oracle_*.py):
+  thermo       -- d(h/R)/dT = cp/R and d(s/R)/dT = cp/(R T) by complex step; continuity at Tmid
+  rates        -- closed-form kinetics (A=B, A->B->C), element conservation, enthalpy
+                  conservation, Gibbs-minimum equilibrium (independent element-potential solve),
+                  detailed balance at equilibrium, fall-off limits (Pr->0, Pr->inf, F(center))
+  jacobian     -- complex-step derivative of rates to 1e-12 row-normwise, central differences
+  integrate    -- Rosenbrock order conditions and L-stability from the coefficient table,
+                  closed-form A=B and A->B->C solutions, observed convergence order
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "chem_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libchem_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+_lp = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C++ compiler (portable flags only)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_load.restype = ctypes.c_void_p
+            lib.oracle_load.argtypes = [ctypes.c_char_p]
+            lib.oracle_free.argtypes = [ctypes.c_void_p]
+            lib.oracle_last_error.restype = ctypes.c_char_p
+            lib.oracle_dims.argtypes = [ctypes.c_void_p, _ip, _ip]
+            lib.oracle_thermo.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, _dp]
+            lib.oracle_thermo_cs.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _dp, _dp]
+            lib.oracle_rates.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, _dp, _dp, _dp, _dp]
+            lib.oracle_reaction_rates.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp,
+                                                  _dp, _dp]
+            lib.oracle_jacobian.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, _dp, _dp, _dp]
+            lib.oracle_jacobian_cs.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _dp, ctypes.c_double,
+                                               _dp]
+            lib.oracle_integrate.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, _dp, _dp,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _ip, _ip, _ip,
+                                             ctypes.c_int, ctypes.c_int]
+            lib.oracle_ros_coefficients.argtypes = [_dp]
+            lib.oracle_opcount.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _dp, _lp]
+            _lib = lib
+    return _lib
+
+
+def _p(a, ptype=_dp):
+    return a.ctypes.data_as(ptype) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class OracleMechanism:
+    """A mechanism file loaded into the oracle."""
+
+    def __init__(self, path: str):
+        self._lib = _load()
+        self._h = self._lib.oracle_load(path.encode())
+        if not self._h:
+            raise RuntimeError("oracle could not load mechanism: " + self._lib.oracle_last_error().decode())
+        K = ctypes.c_int32()
+        R = ctypes.c_int32()
+        self._lib.oracle_dims(self._h, ctypes.byref(K), ctypes.byref(R))
+        self.K, self.R = K.value, R.value
+        self.N = self.K
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.oracle_free(h)
+            self._h = None
+
+    def thermo(self, T: float):
+        out = [np.zeros(self.K) for _ in range(3)]
+        self._lib.oracle_thermo(self._h, float(T), *[_p(o) for o in out])
+        return tuple(out)  # cp/R, h/RT, s/R
+
+    def thermo_cs(self, T: float, step: float = 1e-30):
+        dh = np.zeros(self.K)
+        ds = np.zeros(self.K)
+        self._lib.oracle_thermo_cs(self._h, float(T), step, _p(dh), _p(ds))
+        return dh, ds
+
+    def rates(self, p_Pa: float, T, Y, gross: bool = False):
+        T = _f64(T)
+        Y = _f64(Y)
+        n = T.shape[0]
+        f = np.zeros((self.N, n))
+        g = np.zeros((self.N, n)) if gross else None
+        self._lib.oracle_rates(self._h, float(p_Pa), n, _p(T), _p(Y), _p(f), _p(g))
+        return (f, g) if gross else f
+
+    def reaction_rates(self, p_Pa: float, T: float, Y):
+        Y = _f64(Y)
+        out = [np.zeros(self.R) for _ in range(4)]
+        self._lib.oracle_reaction_rates(self._h, float(p_Pa), float(T), _p(Y), *[_p(o) for o in out])
+        return tuple(out)  # kf, kr, qf, qr
+
+    def jacobian(self, p_Pa: float, T, Y):
+        T = _f64(T)
+        Y = _f64(Y)
+        n = T.shape[0]
+        J = np.zeros((n, self.N, self.N))
+        self._lib.oracle_jacobian(self._h, float(p_Pa), n, _p(T), _p(Y), _p(J))
+        return J
+
+    def jacobian_cs(self, p_Pa: float, T: float, Y, step: float = 1e-30):
+        Y = _f64(Y)
+        J = np.zeros((self.N, self.N))
+        self._lib.oracle_jacobian_cs(self._h, float(p_Pa), float(T), _p(Y), step, _p(J))
+        return J
+
+    def integrate(self, p_Pa: float, T, Y, dt: float, rtol: float = 1e-6, atol: float = 1e-10, h_inout=None,
+                  max_steps: int = 100000, nthreads: int = 1):
+        """Returns (T, Y, status, steps, rejects); inputs are not modified; h_inout is updated in place."""
+        T = _f64(T).copy()
+        Y = _f64(Y).copy()
+        n = T.shape[0]
+        status = np.zeros(n, np.int32)
+        steps = np.zeros(n, np.int32)
+        rej = np.zeros(n, np.int32)
+        if h_inout is not None:
+            assert h_inout.dtype == np.float64 and h_inout.flags.c_contiguous and h_inout.shape == (n,)
+        self._lib.oracle_integrate(self._h, float(p_Pa), n, _p(T), _p(Y), float(dt), float(rtol), float(atol),
+                                   _p(h_inout), _p(status, _ip), _p(steps, _ip), _p(rej, _ip), int(max_steps),
+                                   int(nthreads))
+        return T, Y, status, steps, rej
+
+    def opcount(self, p_Pa: float, T: float, Y):
+        Y = _f64(Y)
+        c = np.zeros(20, np.int64)
+        self._lib.oracle_opcount(self._h, float(p_Pa), float(T), _p(Y), _p(c, _lp))
+        keys = ("add", "mul", "div", "exp", "log")
+        parts = ("rates", "jacobian", "lu", "solve")
+        return {p: dict(zip(keys, c[5 * i:5 * i + 5].tolist())) for i, p in enumerate(parts)}
+
+
+def ros_coefficients():
+    """Classical-form Rosenbrock table used by the oracle: (gamma, alpha[4,4], gamma_ij[4,4], b[4], bhat[4])."""
+    out = np.zeros(41)
+    _load().oracle_ros_coefficients(_p(out))
+    return out[0], out[1:17].reshape(4, 4), out[17:33].reshape(4, 4), out[33:37], out[37:41]

@@ -1,0 +1,841 @@
+// CPU reference ("oracle") for the per-cell finite-rate chemistry solve.
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously-checkable statement of
+// what the GPU library computes.  Only the tests, the smoke check and the benchmark's CPU
+// baseline may build, load or call it; the product path never does.  It shares no code with
+// the CUDA library: it has its own mechanism reader, its own constants and its own
+// formulation of every step.
+//
+// What it computes (paper: Morev et al., "Fast reactive flow simulations using analytical
+// Jacobian and dynamic load balancing in OpenFOAM", Sec. 2.1 Eq. (1) and Sec. 2.3 Eq. (2)):
+//   * per cell, the constant-pressure adiabatic ideal-gas system d(phi)/dt = f(phi),
+//     phi = [T, Y_1 .. Y_{K-1}], Y_K = 1 - sum of the others (Eq. 1);
+//   * f from modified-Arrhenius rates, third-body and Lindemann/Troe fall-off reactions and
+//     reverse rates from NASA-7 Gibbs equilibrium constants (the paper delegates these formulas
+//     to pyJac, Sec. 2.3; the textbook forms used are written next to each function);
+//   * the dense analytical Jacobian J = df/dphi (Sec. 2.3);
+//   * integration over one flow time step with a linearly implicit method (Eq. 2) in its
+//     adaptive Rosenbrock form: 4 stages, order 4 with an embedded order-3 error estimate,
+//     L-stable, partial-pivot LU of (I - gamma h J) (Sec. 2.3: dense LU + back substitution).
+//
+// Everything is scalar FP64 loops in the order the formulas are written.  The scalar type is a
+// template parameter so the same code runs with std::complex<double> (complex-step derivative
+// check of the analytical Jacobian) and with an operation-counting type (the algorithmic FLOP
+// count used by the benchmark's roofline).
+//
+// Units: cgs (mol, cm, s, erg), temperature in K, activation energies in cal/mol.
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <thread>
+#include <vector>
+
+namespace oracle {
+
+// Physical constants (CODATA 2018 gas constant; thermochemical calorie).
+constexpr double kRu = 8.314462618e7;          // erg / (mol K)
+constexpr double kRc = 8.314462618 / 4.184;    // cal / (mol K)
+constexpr double kPatm = 1.01325e6;            // dyn / cm^2
+
+// ----------------------------------------------------------------------------------------------
+// Mechanism
+
+struct Reaction {
+  int type = 0;  // 0 elementary, 1 third body, 2 Lindemann, 3 Troe
+  int reac[2] = {-1, -1};
+  int prod[2] = {-1, -1};
+  double A = 0, b = 0, Ea = 0;      // forward (high-pressure limit for fall-off), Ea in cal/mol
+  double A0 = 0, b0 = 0, Ea0 = 0;   // low-pressure limit (fall-off)
+  double troe[4] = {0, 0, 0, 0};    // alpha, T3, T1, T2
+  std::vector<double> eff;          // collision efficiencies, K entries (types 1-3)
+};
+
+struct Mech {
+  int K = 0, R = 0, E = 0;
+  std::vector<double> W, Tmid;
+  std::vector<std::vector<int>> comp;             // [K][E]
+  std::vector<std::vector<double>> alow, ahigh;   // [K][7]
+  std::vector<Reaction> rx;
+  // net stoichiometric coefficient nu[k][r] = (times k is a product) - (times k is a reactant)
+  std::vector<std::vector<int>> nu;
+};
+
+static bool load_mech(const char* path, Mech& m, std::string& err) {
+  std::ifstream in(path);
+  if (!in) { err = std::string("cannot open ") + path; return false; }
+  std::vector<std::string> lines;
+  std::string line;
+  while (std::getline(in, line)) {
+    size_t p = line.find_first_not_of(" \t\r");
+    if (p == std::string::npos || line[p] == '#') continue;
+    lines.push_back(line);
+  }
+  size_t li = 0;
+  auto next = [&](std::istringstream& ss) -> bool {
+    if (li >= lines.size()) return false;
+    ss.clear();
+    ss.str(lines[li++]);
+    return true;
+  };
+  std::istringstream ss;
+  std::string tok;
+  if (!next(ss) || !(ss >> tok) || tok != "CHEMMECH") { err = "missing CHEMMECH header"; return false; }
+  if (!next(ss) || !(ss >> tok >> m.E) || tok != "elements") { err = "bad elements line"; return false; }
+  for (int e = 0; e < m.E; ++e) next(ss);
+  if (!next(ss) || !(ss >> tok >> m.K) || tok != "species" || m.K < 2) { err = "bad species line"; return false; }
+  m.W.resize(m.K); m.Tmid.resize(m.K);
+  m.comp.assign(m.K, std::vector<int>(m.E));
+  m.alow.assign(m.K, std::vector<double>(7));
+  m.ahigh.assign(m.K, std::vector<double>(7));
+  for (int k = 0; k < m.K; ++k) {
+    double tlo, thi;
+    if (!next(ss) || !(ss >> tok >> m.W[k] >> tlo >> m.Tmid[k] >> thi)) { err = "bad species record"; return false; }
+    for (int e = 0; e < m.E; ++e) ss >> m.comp[k][e];
+    for (int i = 0; i < 7; ++i) ss >> m.alow[k][i];
+    for (int i = 0; i < 7; ++i) ss >> m.ahigh[k][i];
+    if (!ss) { err = "short species record"; return false; }
+  }
+  if (!next(ss) || !(ss >> tok >> m.R) || tok != "reactions" || m.R < 0) { err = "bad reactions line"; return false; }
+  m.rx.resize(m.R);
+  for (int r = 0; r < m.R; ++r) {
+    Reaction& x = m.rx[r];
+    int nr, np;
+    if (!next(ss) || !(ss >> x.type >> nr >> x.reac[0] >> x.reac[1] >> np >> x.prod[0] >> x.prod[1] >> x.A >> x.b >> x.Ea)) {
+      err = "bad reaction record"; return false;
+    }
+    if (x.type >= 1) {
+      if (!next(ss) || !(ss >> tok) || tok != "eff") { err = "missing eff"; return false; }
+      x.eff.resize(m.K);
+      for (int k = 0; k < m.K; ++k) ss >> x.eff[k];
+    }
+    if (x.type >= 2) {
+      if (!next(ss) || !(ss >> tok >> x.A0 >> x.b0 >> x.Ea0) || tok != "low") { err = "missing low"; return false; }
+    }
+    if (x.type == 3) {
+      if (!next(ss) || !(ss >> tok >> x.troe[0] >> x.troe[1] >> x.troe[2] >> x.troe[3]) || tok != "troe") {
+        err = "missing troe"; return false;
+      }
+    }
+  }
+  m.nu.assign(m.K, std::vector<int>(m.R, 0));
+  for (int r = 0; r < m.R; ++r) {
+    for (int s = 0; s < 2; ++s) {
+      if (m.rx[r].reac[s] >= 0) m.nu[m.rx[r].reac[s]][r] -= 1;
+      if (m.rx[r].prod[s] >= 0) m.nu[m.rx[r].prod[s]][r] += 1;
+    }
+  }
+  return true;
+}
+
+// ----------------------------------------------------------------------------------------------
+// Scalar helpers: the same source runs with double, complex<double> and an op-counting type.
+
+inline double re(double x) { return x; }
+inline double re(const std::complex<double>& x) { return x.real(); }
+
+struct OpCounts {
+  int64_t add = 0, mul = 0, div = 0, exp = 0, log = 0;
+};
+static thread_local OpCounts g_ops;
+
+// A double that tallies each arithmetic operation and elementary function call.
+struct Cnt {
+  double v;
+  Cnt(double x = 0.0) : v(x) {}
+};
+inline Cnt operator+(Cnt a, Cnt b) { g_ops.add++; return Cnt(a.v + b.v); }
+inline Cnt operator-(Cnt a, Cnt b) { g_ops.add++; return Cnt(a.v - b.v); }
+inline Cnt operator*(Cnt a, Cnt b) { g_ops.mul++; return Cnt(a.v * b.v); }
+inline Cnt operator/(Cnt a, Cnt b) { g_ops.div++; return Cnt(a.v / b.v); }
+inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
+inline Cnt& operator+=(Cnt& a, Cnt b) { a = a + b; return a; }
+inline Cnt& operator-=(Cnt& a, Cnt b) { a = a - b; return a; }
+inline Cnt& operator*=(Cnt& a, Cnt b) { a = a * b; return a; }
+inline Cnt& operator/=(Cnt& a, Cnt b) { a = a / b; return a; }
+inline Cnt exp(Cnt a) { g_ops.exp++; return Cnt(std::exp(a.v)); }
+inline Cnt log(Cnt a) { g_ops.log++; return Cnt(std::log(a.v)); }
+inline double re(const Cnt& x) { return x.v; }
+
+using std::exp;
+using std::log;
+
+template <class S>
+inline S log10_(const S& x) { return log(x) / S(std::log(10.0)); }
+template <class S>
+inline S pow10_(const S& x) { return exp(x * S(std::log(10.0))); }
+
+// ----------------------------------------------------------------------------------------------
+// Thermodynamics: NASA 7-coefficient polynomials (McBride, Gordon & Reno, NASA TM-4513):
+//   cp/R = a1 + a2 T + a3 T^2 + a4 T^3 + a5 T^4
+//   h/RT = a1 + a2 T/2 + a3 T^2/3 + a4 T^3/4 + a5 T^4/5 + a6/T
+//   s/R  = a1 ln T + a2 T + a3 T^2/2 + a4 T^3/3 + a5 T^4/4 + a7
+// low coefficients for T <= Tmid, high above; no clamping outside the fitted range.
+
+template <class S>
+struct Thermo {
+  std::vector<S> cp_R, h_RT, s_R, dcp_RdT;
+};
+
+template <class S>
+static void thermo(const Mech& m, const S& T, Thermo<S>& th) {
+  th.cp_R.resize(m.K); th.h_RT.resize(m.K); th.s_R.resize(m.K); th.dcp_RdT.resize(m.K);
+  S lnT = log(T);
+  for (int k = 0; k < m.K; ++k) {
+    const std::vector<double>& a = (re(T) <= m.Tmid[k]) ? m.alow[k] : m.ahigh[k];
+    th.cp_R[k] = S(a[0]) + S(a[1]) * T + S(a[2]) * T * T + S(a[3]) * T * T * T + S(a[4]) * T * T * T * T;
+    th.h_RT[k] = S(a[0]) + S(a[1]) * T / S(2.0) + S(a[2]) * T * T / S(3.0) + S(a[3]) * T * T * T / S(4.0) +
+                 S(a[4]) * T * T * T * T / S(5.0) + S(a[5]) / T;
+    th.s_R[k] = S(a[0]) * lnT + S(a[1]) * T + S(a[2]) * T * T / S(2.0) + S(a[3]) * T * T * T / S(3.0) +
+                S(a[4]) * T * T * T * T / S(4.0) + S(a[6]);
+    th.dcp_RdT[k] = S(a[1]) + S(2.0) * S(a[2]) * T + S(3.0) * S(a[3]) * T * T + S(4.0) * S(a[4]) * T * T * T;
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// Rates and the source term f (Eq. 1).
+//
+//   k_f = A T^b exp(-Ea / (Rc T))                                         (modified Arrhenius)
+//   [M] = sum_k eff_k C_k                                                  (third body)
+//   fall-off (Lindemann; Troe form of Gilbert, Luther & Troe 1983, as in the CHEMKIN manual):
+//     Pr = k0 [M] / kinf,   k = kinf Pr/(1+Pr) F
+//     Lindemann F = 1; Troe: Fcent = (1-a) exp(-T/T3) + a exp(-T/T1) + exp(-T2/T),
+//       c = -0.4 - 0.67 log10 Fcent, n = 0.75 - 1.27 log10 Fcent,
+//       f1 = (log10 Pr + c) / (n - 0.14 (log10 Pr + c)),  log10 F = log10 Fcent / (1 + f1^2)
+//   Kc = exp(-sum_k nu_k g_k/RT) (Patm / (Ru T))^(sum_k nu_k),   k_r = k_f / Kc
+//   q = k_f prod C_reac - k_r prod C_prod   (times [M] for third-body reactions)
+//   omega_k = sum_r nu_kr q_r
+//   dT/dt = -sum_k H_k omega_k / (rho cp),  dY_k/dt = W_k omega_k / rho   (k < K)
+
+template <class S>
+struct RateState {
+  S T, rho, Wbar, cp_mass;
+  std::vector<S> Y, C;               // all K species
+  Thermo<S> th;
+  std::vector<S> kf, kr, M, qf, qr, q, omega;
+  // fall-off helpers
+  std::vector<S> Pr, F, dlogF_dlogPr, k0, kinf;
+};
+
+template <class S>
+static void troe_F(const Reaction& x, const S& T, const S& Pr, S& F, S& dlog10F_dlog10Pr) {
+  if (x.type == 2) { F = S(1.0); dlog10F_dlog10Pr = S(0.0); return; }
+  const double a = x.troe[0], T3 = x.troe[1], T1 = x.troe[2], T2 = x.troe[3];
+  S Fcent = S(1.0 - a) * exp(-T / S(T3)) + S(a) * exp(-T / S(T1)) + exp(-S(T2) / T);
+  S L = log10_(Fcent);
+  S c = S(-0.4) - S(0.67) * L;
+  S n = S(0.75) - S(1.27) * L;
+  S x10 = log10_(Pr);
+  S den = n - S(0.14) * (x10 + c);
+  S f1 = (x10 + c) / den;
+  S log10F = L / (S(1.0) + f1 * f1);
+  F = pow10_(log10F);
+  // d f1 / d log10 Pr = n / den^2;  d log10F / d f1 = -2 L f1 / (1 + f1^2)^2
+  dlog10F_dlog10Pr = -S(2.0) * L * f1 / ((S(1.0) + f1 * f1) * (S(1.0) + f1 * f1)) * (n / (den * den));
+}
+
+template <class S>
+static void rates(const Mech& m, double p, const S* phi, S* f, RateState<S>& st) {
+  const int K = m.K, R = m.R;
+  st.T = phi[0];
+  st.Y.resize(K);
+  S ysum = S(0.0);
+  for (int k = 0; k < K - 1; ++k) { st.Y[k] = phi[1 + k]; ysum += st.Y[k]; }
+  st.Y[K - 1] = S(1.0) - ysum;
+  S inv_wbar = S(0.0);
+  for (int k = 0; k < K; ++k) inv_wbar += st.Y[k] / S(m.W[k]);
+  st.Wbar = S(1.0) / inv_wbar;
+  st.rho = S(p) * st.Wbar / (S(kRu) * st.T);
+  st.C.resize(K);
+  for (int k = 0; k < K; ++k) st.C[k] = st.rho * st.Y[k] / S(m.W[k]);
+  thermo(m, st.T, st.th);
+  S lnT = log(st.T);
+  S invT = S(1.0) / st.T;
+  S ln_patm_rut = log(S(kPatm) / (S(kRu) * st.T));
+  st.kf.assign(R, S(0.0)); st.kr.assign(R, S(0.0)); st.M.assign(R, S(0.0));
+  st.qf.assign(R, S(0.0)); st.qr.assign(R, S(0.0)); st.q.assign(R, S(0.0));
+  st.Pr.assign(R, S(0.0)); st.F.assign(R, S(1.0)); st.dlogF_dlogPr.assign(R, S(0.0));
+  st.k0.assign(R, S(0.0)); st.kinf.assign(R, S(0.0));
+  for (int r = 0; r < R; ++r) {
+    const Reaction& x = m.rx[r];
+    S kf = exp(S(std::log(x.A)) + S(x.b) * lnT - S(x.Ea / kRc) * invT);
+    S M = S(0.0);
+    if (x.type >= 1) {
+      for (int k = 0; k < K; ++k) M += S(x.eff[k]) * st.C[k];
+    }
+    if (x.type >= 2) {
+      S k0 = exp(S(std::log(x.A0)) + S(x.b0) * lnT - S(x.Ea0 / kRc) * invT);
+      S Pr = k0 * M / kf;
+      S F, dl;
+      troe_F(x, st.T, Pr, F, dl);
+      st.k0[r] = k0; st.kinf[r] = kf; st.Pr[r] = Pr; st.F[r] = F; st.dlogF_dlogPr[r] = dl;
+      kf = kf * Pr / (S(1.0) + Pr) * F;
+    }
+    // ln Kc = -sum_k nu_k g_k/RT + (sum_k nu_k) ln(Patm/(Ru T))
+    S dG_RT = S(0.0);
+    int dnu = 0;
+    for (int s = 0; s < 2; ++s) {
+      if (x.prod[s] >= 0) { dG_RT += st.th.h_RT[x.prod[s]] - st.th.s_R[x.prod[s]]; dnu += 1; }
+      if (x.reac[s] >= 0) { dG_RT -= st.th.h_RT[x.reac[s]] - st.th.s_R[x.reac[s]]; dnu -= 1; }
+    }
+    S Kc = exp(-dG_RT + S((double)dnu) * ln_patm_rut);
+    S kr = kf / Kc;
+    S pf = S(1.0), pr = S(1.0);
+    for (int s = 0; s < 2; ++s) {
+      if (x.reac[s] >= 0) pf *= st.C[x.reac[s]];
+      if (x.prod[s] >= 0) pr *= st.C[x.prod[s]];
+    }
+    S qf = kf * pf, qr = kr * pr;
+    if (x.type == 1) { qf *= M; qr *= M; }
+    st.kf[r] = kf; st.kr[r] = kr; st.M[r] = M; st.qf[r] = qf; st.qr[r] = qr; st.q[r] = qf - qr;
+  }
+  st.omega.assign(K, S(0.0));
+  for (int k = 0; k < K; ++k)
+    for (int r = 0; r < R; ++r)
+      if (m.nu[k][r] != 0) st.omega[k] += S((double)m.nu[k][r]) * st.q[r];
+  st.cp_mass = S(0.0);
+  for (int k = 0; k < K; ++k) st.cp_mass += st.Y[k] * st.th.cp_R[k] * S(kRu) / S(m.W[k]);
+  S Q = S(0.0);  // sum_k H_k omega_k, erg/(cm^3 s)
+  for (int k = 0; k < K; ++k) Q += st.th.h_RT[k] * S(kRu) * st.T * st.omega[k];
+  f[0] = -Q / (st.rho * st.cp_mass);
+  for (int k = 0; k < K - 1; ++k) f[1 + k] = S(m.W[k]) * st.omega[k] / st.rho;
+}
+
+// ----------------------------------------------------------------------------------------------
+// Analytical Jacobian J[i][j] = d f_i / d phi_j, phi = [T, Y_1..Y_{K-1}] (Sec. 2.3).
+//
+// Chain rule through the concentrations C_j = rho Y_j / W_j, rho = p Wbar/(Ru T),
+// Y_K = 1 - sum_{i<K} Y_i:
+//   d ln rho / dT = -1/T,   d ln rho / dY_i = -Wbar (1/W_i - 1/W_K)
+//   dC_j / dY_i = (rho/W_j)(delta_ij - delta_jK) + C_j d ln rho/dY_i,   dC_j/dT = -C_j/T
+// Per reaction: dq/dC_j (mass action, plus efficiencies through [M]), dq/dT at fixed C.
+// Then with Z_kj = d omega_k / dC_j and Q = sum_k H_k omega_k:
+//   d omega_k/dY_i = (rho/W_i) Z_ki - (rho/W_K) Z_kK + (sum_j Z_kj C_j) d ln rho/dY_i
+//   d omega_k/dT   = d omega_k/dT|_C - (1/T) sum_j Z_kj C_j
+//   f_Yk = W_k omega_k / rho   ->  d f_Yk/dx = (W_k/rho) d omega_k/dx - f_Yk d ln rho/dx
+//   f_T  = -Q/(rho cp)         ->  d f_T/dx  = -(dQ/dx)/(rho cp) - f_T (d ln rho/dx + d ln cp/dx)
+//   dQ/dT = sum_k (cp_k omega_k + H_k d omega_k/dT),  dQ/dY_i = sum_k H_k d omega_k/dY_i
+//   d cp/dY_i = cp_i/W_i - cp_K/W_K (molar cp_k),  d cp/dT = sum_k Y_k (d cp_k/dT)/W_k
+
+template <class S>
+static void jacobian(const Mech& m, double p, const S* phi, S* f, S* J) {
+  const int K = m.K, R = m.R, N = K, d = K - 1;
+  RateState<S> st;
+  rates(m, p, phi, f, st);
+  const S T = st.T, invT = S(1.0) / T;
+  std::vector<S> dlnrho_dY(K - 1);
+  for (int i = 0; i < K - 1; ++i) dlnrho_dY[i] = -st.Wbar * (S(1.0) / S(m.W[i]) - S(1.0) / S(m.W[d]));
+  // Z = d omega / dC (K x K), and dw/dT at fixed C
+  std::vector<S> Z((size_t)K * K, S(0.0)), domega_dT(K, S(0.0));
+  std::vector<S> dqdC(K);
+  for (int r = 0; r < R; ++r) {
+    const Reaction& x = m.rx[r];
+    for (int j = 0; j < K; ++j) dqdC[j] = S(0.0);
+    // mass-action part: d(prod C)/dC_j by the product rule over the two slots
+    auto slot_deriv = [&](const int* sp, const S& kcoef) {
+      if (sp[0] >= 0 && sp[1] >= 0) {
+        dqdC[sp[0]] += kcoef * st.C[sp[1]];
+        dqdC[sp[1]] += kcoef * st.C[sp[0]];
+      } else if (sp[0] >= 0) {
+        dqdC[sp[0]] += kcoef;
+      } else if (sp[1] >= 0) {
+        dqdC[sp[1]] += kcoef;
+      }
+    };
+    S pf = S(1.0), pr = S(1.0);
+    for (int s = 0; s < 2; ++s) {
+      if (x.reac[s] >= 0) pf *= st.C[x.reac[s]];
+      if (x.prod[s] >= 0) pr *= st.C[x.prod[s]];
+    }
+    S mfac = (x.type == 1) ? st.M[r] : S(1.0);
+    slot_deriv(x.reac, mfac * st.kf[r]);
+    slot_deriv(x.prod, -(mfac * st.kr[r]));
+    // d ln kf/dT and d ln Kc/dT at fixed C
+    S dlnkf_dT = S(x.b) * invT + S(x.Ea / kRc) * invT * invT;
+    S dH_RT = S(0.0);
+    int dnu = 0;
+    for (int s = 0; s < 2; ++s) {
+      if (x.prod[s] >= 0) { dH_RT += st.th.h_RT[x.prod[s]]; dnu += 1; }
+      if (x.reac[s] >= 0) { dH_RT -= st.th.h_RT[x.reac[s]]; dnu -= 1; }
+    }
+    // d(g/RT)/dT = -(h/RT)/T  ->  d ln Kc/dT = (sum nu h/RT)/T - (sum nu)/T
+    S dlnKc_dT = (dH_RT - S((double)dnu)) * invT;
+    if (x.type == 1) {
+      S R0 = st.kf[r] * pf - st.kr[r] * pr;
+      for (int j = 0; j < K; ++j) dqdC[j] += S(x.eff[j]) * R0;
+      S dq_dT = st.M[r] * (st.kf[r] * dlnkf_dT * pf - st.kr[r] * (dlnkf_dT - dlnKc_dT) * pr);
+      for (int k = 0; k < K; ++k)
+        if (m.nu[k][r] != 0) domega_dT[k] += S((double)m.nu[k][r]) * dq_dT;
+    } else if (x.type >= 2) {
+      // k = kinf Pr/(1+Pr) F(T, Pr), Pr = k0 [M]/kinf
+      const S Pr = st.Pr[r], F = st.F[r], k0 = st.k0[r];
+      const S dlF = st.dlogF_dlogPr[r];  // d log10 F / d log10 Pr
+      // d k/d[M] = k0 F/(1+Pr) (1/(1+Pr) + d log10F/d log10Pr)
+      S dk_dM = k0 * F / (S(1.0) + Pr) * (S(1.0) / (S(1.0) + Pr) + dlF);
+      S Kc_inv = st.kr[r] / st.kf[r];
+      S R1 = pf - Kc_inv * pr;  // q = k (pf - pr/Kc)
+      for (int j = 0; j < K; ++j) dqdC[j] += S(x.eff[j]) * dk_dM * R1;
+      // d ln k/dT at fixed [M]
+      S dlnkinf_dT = dlnkf_dT;
+      S dlnk0_dT = S(x.b0) * invT + S(x.Ea0 / kRc) * invT * invT;
+      S dlnPr_dT = dlnk0_dT - dlnkinf_dT;
+      S dlnF_dT = S(0.0);
+      if (x.type == 3) {
+        const double a = x.troe[0], T3 = x.troe[1], T1 = x.troe[2], T2 = x.troe[3];
+        S e3 = exp(-T / S(T3)), e1 = exp(-T / S(T1)), e2 = exp(-S(T2) / T);
+        S Fcent = S(1.0 - a) * e3 + S(a) * e1 + e2;
+        S dFcent_dT = -S(1.0 - a) / S(T3) * e3 - S(a) / S(T1) * e1 + S(T2) * invT * invT * e2;
+        S L = log10_(Fcent);
+        S dL_dT = dFcent_dT / (Fcent * S(std::log(10.0)));
+        S c = S(-0.4) - S(0.67) * L, n = S(0.75) - S(1.27) * L;
+        S x10 = log10_(Pr);
+        S den = n - S(0.14) * (x10 + c);
+        S f1 = (x10 + c) / den;
+        S g = S(1.0) + f1 * f1;
+        // d f1 / dL at fixed Pr, with dc/dL = -0.67, dn/dL = -1.27
+        S df1_dL = (S(-0.67) * den - (x10 + c) * (S(-1.27) - S(0.14) * S(-0.67))) / (den * den);
+        S dlog10F_dL = S(1.0) / g - L * S(2.0) * f1 / (g * g) * df1_dL;
+        dlnF_dT = S(std::log(10.0)) * dlog10F_dL * dL_dT;
+      }
+      S dlnk_dT = dlnkinf_dT + (S(1.0) / (S(1.0) + Pr) + dlF) * dlnPr_dT + dlnF_dT;
+      S dq_dT = st.kf[r] * dlnk_dT * pf - st.kr[r] * (dlnk_dT - dlnKc_dT) * pr;
+      for (int k = 0; k < K; ++k)
+        if (m.nu[k][r] != 0) domega_dT[k] += S((double)m.nu[k][r]) * dq_dT;
+    } else {
+      S dq_dT = st.kf[r] * dlnkf_dT * pf - st.kr[r] * (dlnkf_dT - dlnKc_dT) * pr;
+      for (int k = 0; k < K; ++k)
+        if (m.nu[k][r] != 0) domega_dT[k] += S((double)m.nu[k][r]) * dq_dT;
+    }
+    // species with a non-zero dq/dC: the slot species, or every species when [M] enters q
+    std::vector<int> cols;
+    if (x.type >= 1) {
+      for (int j = 0; j < K; ++j) cols.push_back(j);
+    } else {
+      for (int s = 0; s < 2; ++s)
+        for (int sp : {x.reac[s], x.prod[s]})
+          if (sp >= 0 && std::find(cols.begin(), cols.end(), sp) == cols.end()) cols.push_back(sp);
+    }
+    for (int k = 0; k < K; ++k) {
+      if (m.nu[k][r] == 0) continue;
+      S nk = S((double)m.nu[k][r]);
+      for (int j : cols) Z[(size_t)k * K + j] += nk * dqdC[j];
+    }
+  }
+  // d omega_k / dY_i and d omega_k / dT (total)
+  std::vector<S> ZC(K, S(0.0));
+  for (int k = 0; k < K; ++k)
+    for (int j = 0; j < K; ++j) ZC[k] += Z[(size_t)k * K + j] * st.C[j];
+  std::vector<S> dw_dY((size_t)K * (K - 1)), dw_dT(K);
+  for (int k = 0; k < K; ++k) {
+    for (int i = 0; i < K - 1; ++i)
+      dw_dY[(size_t)k * (K - 1) + i] = st.rho / S(m.W[i]) * Z[(size_t)k * K + i] -
+                                       st.rho / S(m.W[d]) * Z[(size_t)k * K + d] + ZC[k] * dlnrho_dY[i];
+    dw_dT[k] = domega_dT[k] - ZC[k] * invT;
+  }
+  // species rows
+  for (int k = 0; k < K - 1; ++k) {
+    J[(size_t)(1 + k) * N + 0] = S(m.W[k]) / st.rho * dw_dT[k] + f[1 + k] * invT;  // -f * dlnrho/dT
+    for (int i = 0; i < K - 1; ++i)
+      J[(size_t)(1 + k) * N + 1 + i] = S(m.W[k]) / st.rho * dw_dY[(size_t)k * (K - 1) + i] - f[1 + k] * dlnrho_dY[i];
+  }
+  // temperature row
+  const S rhocp = st.rho * st.cp_mass;
+  S dQ_dT = S(0.0);
+  for (int k = 0; k < K; ++k) {
+    S Hk = st.th.h_RT[k] * S(kRu) * T;
+    S cpk = st.th.cp_R[k] * S(kRu);
+    dQ_dT += cpk * st.omega[k] + Hk * dw_dT[k];
+  }
+  S dcp_dT = S(0.0);
+  for (int k = 0; k < K; ++k) dcp_dT += st.Y[k] * st.th.dcp_RdT[k] * S(kRu) / S(m.W[k]);
+  J[0] = -dQ_dT / rhocp - f[0] * (-invT + dcp_dT / st.cp_mass);
+  for (int i = 0; i < K - 1; ++i) {
+    S dQ_dYi = S(0.0);
+    for (int k = 0; k < K; ++k) dQ_dYi += st.th.h_RT[k] * S(kRu) * T * dw_dY[(size_t)k * (K - 1) + i];
+    S dcp_dYi = st.th.cp_R[i] * S(kRu) / S(m.W[i]) - st.th.cp_R[d] * S(kRu) / S(m.W[d]);
+    J[1 + i] = -dQ_dYi / rhocp - f[0] * (dlnrho_dY[i] + dcp_dYi / st.cp_mass);
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// Dense LU with partial pivoting (textbook Doolittle, row interchanges; ties go to the lowest
+// row index) and the forward / back substitution that uses it.
+
+template <class S>
+static bool lu_factor(int n, S* a, int* piv) {
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = std::abs(re(a[(size_t)k * n + k]));
+    for (int i = k + 1; i < n; ++i) {
+      double v = std::abs(re(a[(size_t)i * n + k]));
+      if (v > best) { best = v; p = i; }
+    }
+    piv[k] = p;
+    if (best == 0.0) return false;
+    if (p != k)
+      for (int j = 0; j < n; ++j) std::swap(a[(size_t)k * n + j], a[(size_t)p * n + j]);
+    for (int i = k + 1; i < n; ++i) {
+      a[(size_t)i * n + k] = a[(size_t)i * n + k] / a[(size_t)k * n + k];
+      for (int j = k + 1; j < n; ++j) a[(size_t)i * n + j] -= a[(size_t)i * n + k] * a[(size_t)k * n + j];
+    }
+  }
+  return true;
+}
+
+template <class S>
+static void lu_solve(int n, const S* a, const int* piv, S* b) {
+  for (int k = 0; k < n; ++k)
+    if (piv[k] != k) std::swap(b[k], b[piv[k]]);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) b[i] -= a[(size_t)i * n + j] * b[j];
+  for (int i = n - 1; i >= 0; --i) {
+    for (int j = i + 1; j < n; ++j) b[i] -= a[(size_t)i * n + j] * b[j];
+    b[i] = b[i] / a[(size_t)i * n + i];
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// Rosenbrock method, classical form (Hairer & Wanner, Solving ODEs II, Sec. IV.7):
+//   (I - gamma h J) k_i = h f(y + sum_{j<i} alpha_ij k_j) + h J sum_{j<i} gamma_ij k_j
+//   y_new = y + sum b_i k_i,   error = sum (b_i - bhat_i) k_i
+// 4 stages, order 4, embedded order 3, L-stable (R(inf) = 0), R_hat(inf) = 1/2.  gamma is the
+// root near 0.5728 of the order-4 L-stability polynomial; alpha_21 = 2 gamma, alpha_3 = alpha_4
+// = 0.65 (stage 4 reuses stage 3's argument), b_3 = 0, beta_43 = -0.23.  The remaining
+// coefficients solve the order conditions exactly (checked by the tests).
+
+struct Ros4 {
+  static constexpr int s = 4;
+  double gamma = 0.5728160624821348554080014;
+  double alpha[4][4] = {{0, 0, 0, 0},
+                        {1.145632124964269710816, 0, 0, 0},
+                        {0.5153579993305085683839, 0.1346420006694914316161, 0, 0},
+                        {0.5153579993305085683839, 0.1346420006694914316161, 0.0, 0}};
+  double gam[4][4] = {{0, 0, 0, 0},
+                      {-2.341993140193055730037, 0, 0, 0},
+                      {-0.02787068958553465628054, 0.2086236229782045434317, 0, 0},
+                      {-0.2474922550210316401721, -0.1907869111079863467924, -0.23, 0}};
+  double b[4] = {0.3189845243949336284427, 0.05124233729027201389922, 0.0, 0.6297731383147943576581};
+  double bhat[4] = {0.04912862293304546304649, -0.07686730508695069897692, -0.1719498044983180858675,
+                    1.199688486652223321798};
+};
+
+enum Status { kOk = 0, kMaxSteps = 1, kHUnderflow = 2, kBadInput = 3 };
+
+struct CellStats {
+  int64_t steps = 0, rejects = 0, f_evals = 0, lu = 0;
+};
+
+// Step-size controller (paper Sec. 2.3: adaptive sub-steps under rtol/atol; formula from
+// Hairer & Wanner IV.8):  e = (I - gamma h J)^-1 sum (b_i - bhat_i) k_i (filtered estimate),
+// err = max_i |e_i| / (atol + rtol max(|y_i|, |ynew_i|));
+// accept if err <= 1; h_new = h min(facmax, max(0.2, 0.9 err^(-1/4))), facmax = 6, or 1 on the
+// step after a rejection.  Non-finite err or a singular pivot counts as a rejection with factor
+// 0.2.  The last step is clipped so that t reaches dt exactly.  The cold-start step is
+// 0.01 dt; a positive h_inout overrides it (carry-over of the chemistry sub-step, Sec. 2.3).
+static int integrate_cell(const Mech& m, double p, double* phi, double dt, double rtol, double atol, double* h_io,
+                          int max_steps, CellStats& cs) {
+  const int N = m.K;
+  if (!(std::isfinite(phi[0]) && phi[0] > 0.0)) return kBadInput;
+  for (int i = 1; i < N; ++i)
+    if (!std::isfinite(phi[i])) return kBadInput;
+  Ros4 c;
+  std::vector<double> y(phi, phi + N), ynew(N), f0(N), fi(N), J((size_t)N * N), A((size_t)N * N), yi(N), g(N),
+      rhs(N), err(N);
+  std::vector<std::vector<double>> k(4, std::vector<double>(N));
+  std::vector<int> piv(N);
+  double h = (h_io && *h_io > 0.0) ? std::min(*h_io, dt) : 0.01 * dt;
+  double t = 0.0;
+  bool need_jac = true, last_rejected = false;
+  double h_next_unclipped = h;
+  int status = kOk;
+  for (int attempt = 0;; ++attempt) {
+    if (attempt >= max_steps) { status = kMaxSteps; break; }
+    if (h_next_unclipped < 1e-14 * dt) { status = kHUnderflow; break; }
+    if (need_jac) {
+      jacobian(m, p, y.data(), f0.data(), J.data());
+      cs.f_evals++;
+      need_jac = false;
+    }
+    for (size_t e = 0; e < (size_t)N * N; ++e) A[e] = -c.gamma * h * J[e];
+    for (int i = 0; i < N; ++i) A[(size_t)i * N + i] += 1.0;
+    bool ok = lu_factor(N, A.data(), piv.data());
+    cs.lu++;
+    double errn = INFINITY;
+    if (ok) {
+      for (int s = 0; s < 4; ++s) {
+        for (int i = 0; i < N; ++i) {
+          yi[i] = y[i];
+          g[i] = 0.0;
+          for (int j = 0; j < s; ++j) { yi[i] += c.alpha[s][j] * k[j][i]; g[i] += c.gam[s][j] * k[j][i]; }
+        }
+        if (s == 0) {
+          fi = f0;
+        } else {
+          RateState<double> st;
+          rates(m, p, yi.data(), fi.data(), st);
+          cs.f_evals++;
+        }
+        for (int i = 0; i < N; ++i) {
+          double jg = 0.0;
+          for (int j = 0; j < N; ++j) jg += J[(size_t)i * N + j] * g[j];
+          rhs[i] = h * fi[i] + h * jg;
+        }
+        lu_solve(N, A.data(), piv.data(), rhs.data());
+        k[s] = rhs;
+      }
+      for (int i = 0; i < N; ++i) {
+        double yn = y[i], e = 0.0;
+        for (int s = 0; s < 4; ++s) { yn += c.b[s] * k[s][i]; e += (c.b[s] - c.bhat[s]) * k[s][i]; }
+        ynew[i] = yn;
+        err[i] = e;
+      }
+      // error filter: the embedded difference is passed through (I - gamma h J)^-1, which leaves
+      // non-stiff components unchanged and damps stiff ones, whose raw estimate does not shrink
+      // with h because R_hat(inf) != 0 (Shampine; Hairer & Wanner IV.8)
+      lu_solve(N, A.data(), piv.data(), err.data());
+      errn = 0.0;
+      for (int i = 0; i < N; ++i) {
+        double sc = atol + rtol * std::max(std::fabs(y[i]), std::fabs(ynew[i]));
+        double r = std::fabs(err[i]) / sc;
+        if (!(r <= errn)) errn = r;  // propagates NaN
+      }
+    }
+    double fac;
+    if (std::isfinite(errn) && errn <= 1.0) {
+      t = (h >= dt - t) ? dt : t + h;
+      y = ynew;
+      cs.steps++;
+      need_jac = true;
+      fac = std::min(6.0, std::max(0.2, 0.9 * std::pow(errn, -0.25)));
+      if (last_rejected) fac = std::min(fac, 1.0);
+      last_rejected = false;
+      h_next_unclipped = h * fac;
+      if (t >= dt) break;
+    } else {
+      cs.rejects++;
+      fac = std::isfinite(errn) ? std::max(0.2, 0.9 * std::pow(errn, -0.25)) : 0.2;
+      fac = std::min(fac, 1.0);
+      last_rejected = true;
+      h_next_unclipped = h * fac;
+    }
+    h = std::min(h_next_unclipped, dt - t);
+  }
+  for (int i = 0; i < N; ++i) phi[i] = y[i];
+  if (h_io) *h_io = h_next_unclipped;
+  return status;
+}
+
+}  // namespace oracle
+
+// ==============================================================================================
+// C interface for the tests and the benchmark's CPU baseline.
+
+using namespace oracle;
+
+static thread_local std::string g_err;
+
+extern "C" {
+
+const char* oracle_last_error() { return g_err.c_str(); }
+
+void* oracle_load(const char* path) {
+  Mech* m = new Mech();
+  if (!load_mech(path, *m, g_err)) { delete m; return nullptr; }
+  return m;
+}
+
+void oracle_free(void* h) { delete static_cast<Mech*>(h); }
+
+int oracle_dims(void* h, int* K, int* R) {
+  Mech* m = static_cast<Mech*>(h);
+  *K = m->K; *R = m->R;
+  return 0;
+}
+
+// Species thermo at one temperature: cp/R, h/RT, s/R (K each).
+int oracle_thermo(void* h, double T, double* cp_R, double* h_RT, double* s_R) {
+  Mech* m = static_cast<Mech*>(h);
+  Thermo<double> th;
+  thermo(*m, T, th);
+  for (int k = 0; k < m->K; ++k) { cp_R[k] = th.cp_R[k]; h_RT[k] = th.h_RT[k]; s_R[k] = th.s_R[k]; }
+  return 0;
+}
+
+// d/dT of h/RT*T (=h/R) and s/R by complex step, for the thermo consistency pins.
+int oracle_thermo_cs(void* h, double T, double step, double* dhR_dT, double* dsR_dT) {
+  Mech* m = static_cast<Mech*>(h);
+  using C = std::complex<double>;
+  Thermo<C> th;
+  C Tc(T, step);
+  thermo(*m, Tc, th);
+  for (int k = 0; k < m->K; ++k) {
+    dhR_dT[k] = (th.h_RT[k] * Tc).imag() / step;
+    dsR_dT[k] = th.s_R[k].imag() / step;
+  }
+  return 0;
+}
+
+// f for n cells.  p in Pa.  T[n], Y[K][n] species-major (all K species; Y_K is recomputed
+// from the others as in Eq. 1), out f[N][n].  Optional per-cell gross scale
+// gross[N][n] = |.| sums of the forward and reverse fluxes entering each component.
+int oracle_rates(void* h, double p_Pa, int64_t n, const double* T, const double* Y, double* f, double* gross) {
+  Mech* m = static_cast<Mech*>(h);
+  const int K = m->K, N = K;
+  const double p = p_Pa * 10.0;
+  std::vector<double> phi(N), fo(N);
+  for (int64_t c = 0; c < n; ++c) {
+    phi[0] = T[c];
+    for (int k = 0; k < K - 1; ++k) phi[1 + k] = Y[(size_t)k * n + c];
+    RateState<double> st;
+    rates(*m, p, phi.data(), fo.data(), st);
+    for (int i = 0; i < N; ++i) f[(size_t)i * n + c] = fo[i];
+    if (gross) {
+      std::vector<double> gk(K, 0.0);
+      double gT = 0.0;
+      for (int r = 0; r < m->R; ++r)
+        for (int k = 0; k < K; ++k)
+          if (m->nu[k][r] != 0) {
+            double a = std::abs((double)m->nu[k][r]) * (std::fabs(st.qf[r]) + std::fabs(st.qr[r]));
+            gk[k] += a;
+            gT += std::fabs(st.th.h_RT[k] * kRu * st.T) * a;
+          }
+      gross[c] = gT / (st.rho * st.cp_mass);
+      for (int k = 0; k < K - 1; ++k) gross[(size_t)(1 + k) * n + c] = m->W[k] * gk[k] / st.rho;
+    }
+  }
+  return 0;
+}
+
+// Per-reaction quantities at one state (tests): kf, kr (effective), qf, qr, and ln Kc.
+int oracle_reaction_rates(void* h, double p_Pa, double T, const double* Y, double* kf, double* kr, double* qf,
+                          double* qr) {
+  Mech* m = static_cast<Mech*>(h);
+  const int K = m->K;
+  std::vector<double> phi(K), fo(K);
+  phi[0] = T;
+  for (int k = 0; k < K - 1; ++k) phi[1 + k] = Y[k];
+  RateState<double> st;
+  rates(*m, p_Pa * 10.0, phi.data(), fo.data(), st);
+  for (int r = 0; r < m->R; ++r) { kf[r] = st.kf[r]; kr[r] = st.kr[r]; qf[r] = st.qf[r]; qr[r] = st.qr[r]; }
+  return 0;
+}
+
+// Analytical Jacobian for n cells: J[n][N][N], row i = d f_i.
+int oracle_jacobian(void* h, double p_Pa, int64_t n, const double* T, const double* Y, double* J) {
+  Mech* m = static_cast<Mech*>(h);
+  const int K = m->K, N = K;
+  std::vector<double> phi(N), fo(N);
+  for (int64_t c = 0; c < n; ++c) {
+    phi[0] = T[c];
+    for (int k = 0; k < K - 1; ++k) phi[1 + k] = Y[(size_t)k * n + c];
+    jacobian(*m, p_Pa * 10.0, phi.data(), fo.data(), J + (size_t)c * N * N);
+  }
+  return 0;
+}
+
+// Complex-step Jacobian of f at one state: Jcs[N][N] with Jcs[i][j] = Im f_i(phi + i h e_j)/h.
+int oracle_jacobian_cs(void* h, double p_Pa, double T, const double* Y, double step, double* Jcs) {
+  Mech* m = static_cast<Mech*>(h);
+  const int K = m->K, N = K;
+  using C = std::complex<double>;
+  std::vector<C> phi(N), fo(N);
+  for (int j = 0; j < N; ++j) {
+    phi[0] = C(T, 0.0);
+    for (int k = 0; k < K - 1; ++k) phi[1 + k] = C(Y[k], 0.0);
+    phi[j] += C(0.0, step);
+    RateState<C> st;
+    rates(*m, p_Pa * 10.0, phi.data(), fo.data(), st);
+    for (int i = 0; i < N; ++i) Jcs[(size_t)i * N + j] = fo[i].imag() / step;
+  }
+  return 0;
+}
+
+// Integrate n cells over dt.  T[n] and Y[K][n] are updated in place (Y_K = 1 - sum of the
+// others on output).  h_inout[n] may be NULL.  status[n], steps[n], rejects[n] may be NULL.
+int oracle_integrate(void* h, double p_Pa, int64_t n, double* T, double* Y, double dt, double rtol, double atol,
+                     double* h_inout, int32_t* status, int32_t* steps, int32_t* rejects, int max_steps, int nthreads) {
+  Mech* m = static_cast<Mech*>(h);
+  const int K = m->K, N = K;
+  if (nthreads < 1) nthreads = 1;
+  std::atomic<int64_t> next(0);
+  auto work = [&]() {
+    std::vector<double> phi(N);
+    for (;;) {
+      int64_t c = next.fetch_add(1);
+      if (c >= n) break;
+      phi[0] = T[c];
+      for (int k = 0; k < K - 1; ++k) phi[1 + k] = Y[(size_t)k * n + c];
+      CellStats cs;
+      int st = integrate_cell(*m, p_Pa * 10.0, phi.data(), dt, rtol, atol, h_inout ? &h_inout[c] : nullptr,
+                              max_steps, cs);
+      T[c] = phi[0];
+      double ysum = 0.0;
+      for (int k = 0; k < K - 1; ++k) { Y[(size_t)k * n + c] = phi[1 + k]; ysum += phi[1 + k]; }
+      Y[(size_t)(K - 1) * n + c] = 1.0 - ysum;
+      if (status) status[c] = st;
+      if (steps) steps[c] = (int32_t)cs.steps;
+      if (rejects) rejects[c] = (int32_t)cs.rejects;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nthreads; ++t) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
+  return 0;
+}
+
+// Rosenbrock coefficient table (classical form), for the order-condition tests:
+// out = [gamma, alpha (16, row-major), gamma_ij (16), b (4), bhat (4)].
+int oracle_ros_coefficients(double* out) {
+  Ros4 c;
+  out[0] = c.gamma;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) { out[1 + i * 4 + j] = c.alpha[i][j]; out[17 + i * 4 + j] = c.gam[i][j]; }
+  for (int i = 0; i < 4; ++i) { out[33 + i] = c.b[i]; out[37 + i] = c.bhat[i]; }
+  return 0;
+}
+
+// Algorithmic operation counts of one rate evaluation, one Jacobian evaluation, one LU factor
+// and one LU solve at the given state.  counts[5 * 4] = {add, mul, div, exp, log} for
+// [rates, jacobian (including its own rate evaluation), lu, solve].
+int oracle_opcount(void* h, double p_Pa, double T, const double* Y, int64_t* counts) {
+  Mech* m = static_cast<Mech*>(h);
+  const int K = m->K, N = K;
+  std::vector<Cnt> phi(N), fo(N), J((size_t)N * N);
+  phi[0] = Cnt(T);
+  for (int k = 0; k < K - 1; ++k) phi[1 + k] = Cnt(Y[k]);
+  auto dump = [&](int slot) {
+    counts[slot * 5 + 0] = g_ops.add; counts[slot * 5 + 1] = g_ops.mul; counts[slot * 5 + 2] = g_ops.div;
+    counts[slot * 5 + 3] = g_ops.exp; counts[slot * 5 + 4] = g_ops.log;
+    g_ops = OpCounts();
+  };
+  g_ops = OpCounts();
+  {
+    RateState<Cnt> st;
+    rates(*m, p_Pa * 10.0, phi.data(), fo.data(), st);
+  }
+  dump(0);
+  jacobian(*m, p_Pa * 10.0, phi.data(), fo.data(), J.data());
+  dump(1);
+  // LU and a solve on W = I/(gamma h) - J's pattern: use the identity-shifted Jacobian itself
+  std::vector<Cnt> A(J);
+  for (int i = 0; i < N; ++i) A[(size_t)i * N + i] = A[(size_t)i * N + i] + Cnt(1e6);
+  g_ops = OpCounts();
+  std::vector<int> piv(N);
+  lu_factor(N, A.data(), piv.data());
+  dump(2);
+  std::vector<Cnt> b(N, Cnt(1.0));
+  lu_solve(N, A.data(), piv.data(), b.data());
+  dump(3);
+  return 0;
+}
+
+}  // extern "C"
