@@ -1,0 +1,120 @@
+/*
+ * chemgpu: GB300 (sm_103a) batched finite-rate chemistry solve -- C ABI.
+ *
+ * The operation (Morev et al., "Fast reactive flow simulations using analytical Jacobian and
+ * dynamic load balancing in OpenFOAM"): for every CFD cell, integrate the stiff
+ * constant-pressure ideal-gas system d(phi)/dt = f(phi), phi = [T, Y_1 .. Y_{K-1}]
+ * (Sec. 2.1, Eq. 1), over one flow time step dt, with a linearly implicit method (Sec. 2.3,
+ * Eq. 2) in adaptive Rosenbrock form, using the analytical Jacobian of f and a dense LU of the
+ * iteration matrix (Sec. 2.3).  Y_K = 1 - sum of the others (Eq. 1).
+ *
+ * Conventions shared by all entry points
+ *   - Units at the boundary: T in K, p in Pa, dt in s, mass fractions dimensionless; internal
+ *     arithmetic is cgs.  The rate outputs are in K/s and 1/s.
+ *   - Cell arrays are species-major: Y[k * ncells + c] for species k of cell c, all K species.
+ *   - Array pointers may be device pointers (the call is asynchronous on `stream`, results valid
+ *     after the stream is synchronised) or host pointers, pageable or pinned (the library copies
+ *     through its own device workspace with cudaMemcpyAsync on `stream`, then synchronises the
+ *     stream before returning).  All arrays of one call must be of the same kind.  The caller
+ *     owns every array; the library owns the mechanism handle and its workspaces.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   - Return value: 0 on success; a negative CHEM_E* code on invalid arguments or a CUDA error,
+ *     with a message in chem_last_error() (thread-local).  No exception crosses the ABI and no
+ *     kernel traps: per-cell numerical failure is reported in status[], not as a call failure.
+ *   - A mechanism handle may be used from one host thread at a time.
+ */
+#ifndef CHEMGPU_H
+#define CHEMGPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define CHEM_OK 0
+#define CHEM_EINVAL (-1)   /* bad argument (NULL, ncells < 0, dt <= 0, rtol <= 0, ...) */
+#define CHEM_EFILE (-2)    /* mechanism file unreadable or malformed */
+#define CHEM_ECUDA (-3)    /* a CUDA runtime call failed */
+#define CHEM_ESIZE (-4)    /* mechanism too large for the kernels' shared-memory plan */
+
+/* per-cell status written by chem_integrate (the cell keeps its last accepted state) */
+#define CHEM_CELL_OK 0
+#define CHEM_CELL_MAX_STEPS 1    /* step-attempt limit reached before t = dt */
+#define CHEM_CELL_H_UNDERFLOW 2  /* proposed step fell below 1e-14 dt */
+#define CHEM_CELL_BAD_INPUT 3    /* non-finite input or T <= 0; state left unchanged */
+
+/* precision of the linear solves inside the Rosenbrock stages */
+#define CHEM_PREC_FP64 0   /* FP64 LU and substitutions */
+#define CHEM_PREC_MIXED 1  /* FP32 LU + FP64-residual iterative refinement; rates, Kc, error
+                              norm, step control and state update stay FP64 */
+
+typedef struct chem_mech chem_mech; /* opaque */
+
+typedef struct {
+  int precision;     /* CHEM_PREC_FP64 (default) or CHEM_PREC_MIXED */
+  int refine_sweeps; /* mixed: FP64-residual refinement sweeps per stage solve (default 2, 1..4) */
+  int max_steps;     /* step attempts per cell per call (default 100000) */
+  int use_queue;     /* 1 (default): persistent kernel pulling cells from a device work queue;
+                        0: static round-robin assignment of cells to warps */
+  int cells_per_cta; /* warps (cells in flight) per CTA; 0 = automatic */
+  int ctas_per_sm;   /* resident CTAs per SM for the persistent grid; 0 = automatic */
+} chem_opts;
+
+typedef struct {
+  int64_t steps;        /* accepted steps, summed over cells */
+  int64_t rejects;      /* rejected step attempts */
+  int64_t failed_cells; /* cells whose status is not CHEM_CELL_OK */
+  int64_t refine_fallbacks; /* mixed precision: stage solves that fell back to an FP64 factor */
+} chem_stats;
+
+/* Fill `opts` with the defaults. */
+void chem_default_opts(chem_opts* opts);
+
+/* Load a mechanism file (text format written by the synthetic generator: elements, species
+ * with molar mass and NASA 7-coefficient polynomials, reversible reactions of type elementary,
+ * third-body, Lindemann or Troe fall-off) and upload its tables to the current CUDA device.
+ * On success *out owns the tables until chem_free_mechanism. */
+int chem_load_mechanism(const char* path, chem_mech** out);
+void chem_free_mechanism(chem_mech* mech);
+
+/* Number of species K (= state length N) and reactions R. */
+int chem_mech_dims(const chem_mech* mech, int* K, int* R);
+
+/* Source term f of Eq. 1 for ncells cells at pressure p_Pa:
+ *   dPhidt[0 * ncells + c] = dT/dt, dPhidt[(1 + k) * ncells + c] = dY_k/dt for k < K-1.
+ * T[ncells], Y[K * ncells] as above (Y_K is recomputed as 1 - sum of the others). */
+int chem_rates(const chem_mech* mech, double p_Pa, const double* T, const double* Y, int64_t ncells,
+               double* dPhidt, void* stream);
+
+/* Analytical Jacobian J = df/dphi (Sec. 2.3) for ncells cells:
+ *   J[c * N * N + i * N + j] = d f_i / d phi_j, phi = [T, Y_1 .. Y_{K-1}], N = K. */
+int chem_jacobian(const chem_mech* mech, double p_Pa, const double* T, const double* Y, int64_t ncells,
+                  double* J, void* stream);
+
+/* Integrate every cell over [0, dt] (Sec. 2.1 Eq. 1; Sec. 2.3 Eq. 2 and the adaptive sub-steps
+ * with carry-over).  T[ncells] and Y[K * ncells] are read and overwritten with the state at dt.
+ * h_inout[ncells] (may be NULL): on entry a positive value is the first sub-step to try
+ * (else 0.01 dt); on exit the controller's next proposed sub-step, for the next call.
+ * status[ncells] (may be NULL): CHEM_CELL_* per cell.
+ * opts may be NULL (defaults); stats may be NULL; when given, the call synchronises `stream`
+ * to read the totals back. */
+int chem_integrate(const chem_mech* mech, double p_Pa, double* T, double* Y, int64_t ncells, double dt,
+                   double rtol, double atol, double* h_inout, int32_t* status, const chem_opts* opts,
+                   chem_stats* stats, void* stream);
+
+/* Per-cell counters of the last chem_integrate on this mechanism handle, copied to the
+ * caller's arrays (device or host, ncells entries each, either may be NULL).  Valid until the
+ * next chem_integrate on the handle. */
+int chem_last_cell_counters(const chem_mech* mech, int32_t* steps, int32_t* rejects, int64_t ncells,
+                            void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* chem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHEMGPU_H */

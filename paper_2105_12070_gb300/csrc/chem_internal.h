@@ -1,0 +1,63 @@
+// Internal layout shared by the host table builder (mech_tables.cpp) and the kernels
+// (chem_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace chemgpu {
+
+// Reaction kinds in device order: all elementary reactions first, then third-body, then
+// fall-off (Lindemann and Troe), so that lanes of one warp pass mostly run the same branch.
+enum : int { kElementary = 0, kThirdBody = 1, kLindemann = 2, kTroe = 3 };
+
+// Per-reaction integer record (16 ints).
+//   [0..3]  slot species: reactant 0, reactant 1, product 0, product 1 (-1 = empty)
+//   [4..7]  distinct slot species (the columns where dq/dC is non-zero without [M]), -1 pads
+//   [8..11] rows: distinct species k < K-1 with non-zero net coefficient, -1 pads
+//   [12..15] net coefficients of those rows
+constexpr int kRxInts = 16;
+
+// Per-reaction double record.
+//   [0] ln A   [1] b   [2] Ea/Rc (K)
+constexpr int kRxDoubles = 3;
+
+// Per fall-off reaction doubles: ln A0, b0, Ea0/Rc, alpha, T3, T1, T2, is_troe
+constexpr int kFoDoubles = 8;
+
+// Per species doubles: W, 1/W, Tmid, NASA low a1..a7, NASA high a1..a7
+constexpr int kSpDoubles = 17;
+
+struct HostMech {
+  int K = 0, R = 0, E = 0;
+  int n_elem = 0, n_tb = 0, n_fo = 0;  // counts in device order
+  std::vector<int> order;              // device reaction index -> file reaction index
+  std::vector<double> sp;              // [K][kSpDoubles]
+  std::vector<double> rxd;             // [R][kRxDoubles]
+  std::vector<int> rxi;                // [R][kRxInts]
+  std::vector<int> dnu;                // [R] products minus reactants
+  std::vector<double> eff;             // [n_tb + n_fo][K]
+  std::vector<double> fo;              // [n_fo][kFoDoubles]
+  // species -> (reaction, net coefficient) lists, all K species: entry = r * 8 + (nu + 4)
+  std::vector<int> sr_ptr;             // [K + 1]
+  std::vector<int> sr_idx;
+};
+
+// Parse the mechanism text file; false + message on error.
+bool parse_mechanism(const char* path, HostMech& m, std::string& err);
+
+// Device view of the tables (all pointers into one device allocation).
+struct DevMech {
+  int K, R, N;
+  int n_elem, n_tb, n_fo, n_pd;  // n_pd = n_tb + n_fo; PD reactions are indices n_elem .. R-1
+  const double* sp;
+  const double* rxd;
+  const int* rxi;
+  const int* dnu;
+  const double* eff;
+  const double* fo;
+  const int* sr_ptr;
+  const int* sr_idx;
+};
+
+}  // namespace chemgpu

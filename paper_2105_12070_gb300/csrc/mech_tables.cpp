@@ -1,0 +1,209 @@
+// Mechanism file reader and device-table builder (host side of chem_load_mechanism).
+//
+// File format: see the generator (synth.py).  Species carry molar mass and NASA-7
+// polynomials; reactions are reversible, with up to two reactants and two products, of type
+// elementary, third-body, Lindemann or Troe fall-off (Sec. 2.3 delegates these forms to the
+// mechanism; the tables here only re-arrange them for the kernels).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "chem_internal.h"
+
+namespace chemgpu {
+
+namespace {
+
+constexpr double kRcal = 8.314462618 / 4.184;  // cal/(mol K)
+
+struct Reader {
+  FILE* f = nullptr;
+  char line[1 << 16];
+  char* cur = nullptr;
+  bool next_line() {
+    while (std::fgets(line, sizeof(line), f)) {
+      char* p = line;
+      while (*p == ' ' || *p == '\t') ++p;
+      if (*p == '#' || *p == '\n' || *p == '\r' || *p == 0) continue;
+      cur = p;
+      return true;
+    }
+    return false;
+  }
+  bool word(char* out, size_t n) {
+    while (*cur == ' ' || *cur == '\t') ++cur;
+    size_t i = 0;
+    while (*cur && *cur != ' ' && *cur != '\t' && *cur != '\n' && *cur != '\r' && i + 1 < n) out[i++] = *cur++;
+    out[i] = 0;
+    return i > 0;
+  }
+  bool num(double& v) {
+    char* end;
+    v = std::strtod(cur, &end);
+    if (end == cur) return false;
+    cur = end;
+    return true;
+  }
+  bool inum(int& v) {
+    char* end;
+    long x = std::strtol(cur, &end, 10);
+    if (end == cur) return false;
+    cur = end;
+    v = (int)x;
+    return true;
+  }
+};
+
+struct FileReaction {
+  int type = 0, reac[2] = {-1, -1}, prod[2] = {-1, -1};
+  double A = 0, b = 0, Ea = 0, A0 = 0, b0 = 0, Ea0 = 0, troe[4] = {0, 0, 0, 0};
+  std::vector<double> eff;
+};
+
+}  // namespace
+
+bool parse_mechanism(const char* path, HostMech& m, std::string& err) {
+  Reader rd;
+  rd.f = std::fopen(path, "r");
+  if (!rd.f) { err = std::string("cannot open mechanism file ") + path; return false; }
+  struct Closer { FILE* f; ~Closer() { std::fclose(f); } } closer{rd.f};
+  char w[64];
+  auto fail = [&](const char* what) { err = std::string("mechanism ") + path + ": " + what; return false; };
+  if (!rd.next_line() || !rd.word(w, sizeof w) || std::strcmp(w, "CHEMMECH")) return fail("missing CHEMMECH header");
+  if (!rd.next_line() || !rd.word(w, sizeof w) || std::strcmp(w, "elements") || !rd.inum(m.E) || m.E < 1)
+    return fail("bad elements line");
+  for (int e = 0; e < m.E; ++e)
+    if (!rd.next_line()) return fail("short element list");
+  if (!rd.next_line() || !rd.word(w, sizeof w) || std::strcmp(w, "species") || !rd.inum(m.K) || m.K < 2)
+    return fail("bad species line");
+  const int K = m.K;
+  m.sp.assign((size_t)K * kSpDoubles, 0.0);
+  for (int k = 0; k < K; ++k) {
+    double W, tlo, tmid, thi, a;
+    if (!rd.next_line() || !rd.word(w, sizeof w) || !rd.num(W) || !rd.num(tlo) || !rd.num(tmid) || !rd.num(thi))
+      return fail("bad species record");
+    for (int e = 0; e < m.E; ++e) {
+      int c;
+      if (!rd.inum(c)) return fail("bad composition");
+    }
+    if (!(W > 0)) return fail("non-positive molar mass");
+    double* s = &m.sp[(size_t)k * kSpDoubles];
+    s[0] = W;
+    s[1] = 1.0 / W;
+    s[2] = tmid;
+    for (int i = 0; i < 14; ++i) {
+      if (!rd.num(a)) return fail("short NASA coefficients");
+      s[3 + i] = a;
+    }
+  }
+  int R;
+  if (!rd.next_line() || !rd.word(w, sizeof w) || std::strcmp(w, "reactions") || !rd.inum(R) || R < 0)
+    return fail("bad reactions line");
+  std::vector<FileReaction> rx(R);
+  for (int r = 0; r < R; ++r) {
+    FileReaction& x = rx[r];
+    int nr, np;
+    if (!rd.next_line() || !rd.inum(x.type) || !rd.inum(nr) || !rd.inum(x.reac[0]) || !rd.inum(x.reac[1]) ||
+        !rd.inum(np) || !rd.inum(x.prod[0]) || !rd.inum(x.prod[1]) || !rd.num(x.A) || !rd.num(x.b) || !rd.num(x.Ea))
+      return fail("bad reaction record");
+    if (x.type < 0 || x.type > 3) return fail("unknown reaction type");
+    for (int s = 0; s < 2; ++s)
+      if (x.reac[s] < -1 || x.reac[s] >= K || x.prod[s] < -1 || x.prod[s] >= K) return fail("species index out of range");
+    if ((x.reac[0] < 0 && x.reac[1] < 0) || (x.prod[0] < 0 && x.prod[1] < 0)) return fail("empty reaction side");
+    // the kernels expect slot 0 of each side to be filled
+    if (x.reac[0] < 0) std::swap(x.reac[0], x.reac[1]);
+    if (x.prod[0] < 0) std::swap(x.prod[0], x.prod[1]);
+    if (!(x.A > 0)) return fail("non-positive pre-exponential factor");
+    if (x.type >= 1) {
+      if (!rd.next_line() || !rd.word(w, sizeof w) || std::strcmp(w, "eff")) return fail("missing eff line");
+      x.eff.resize(K);
+      for (int k = 0; k < K; ++k)
+        if (!rd.num(x.eff[k])) return fail("short eff line");
+    }
+    if (x.type >= 2) {
+      if (!rd.next_line() || !rd.word(w, sizeof w) || std::strcmp(w, "low") || !rd.num(x.A0) || !rd.num(x.b0) ||
+          !rd.num(x.Ea0))
+        return fail("missing low line");
+      if (!(x.A0 > 0)) return fail("non-positive low-pressure factor");
+    }
+    if (x.type == 3) {
+      if (!rd.next_line() || !rd.word(w, sizeof w) || std::strcmp(w, "troe") || !rd.num(x.troe[0]) ||
+          !rd.num(x.troe[1]) || !rd.num(x.troe[2]) || !rd.num(x.troe[3]))
+        return fail("missing troe line");
+    }
+  }
+  // device order: elementary, third-body, Lindemann, Troe (stable within each kind)
+  m.R = R;
+  m.order.clear();
+  for (int t = 0; t <= 3; ++t)
+    for (int r = 0; r < R; ++r)
+      if (rx[r].type == t) m.order.push_back(r);
+  m.n_elem = m.n_tb = m.n_fo = 0;
+  for (int r = 0; r < R; ++r) {
+    if (rx[r].type == kElementary) m.n_elem++;
+    else if (rx[r].type == kThirdBody) m.n_tb++;
+    else m.n_fo++;
+  }
+  m.rxd.assign((size_t)R * kRxDoubles, 0.0);
+  m.rxi.assign((size_t)R * kRxInts, -1);
+  m.dnu.assign(R, 0);
+  m.eff.assign((size_t)(m.n_tb + m.n_fo) * K, 0.0);
+  m.fo.assign((size_t)m.n_fo * kFoDoubles, 0.0);
+  std::vector<std::vector<int>> sr(K);
+  for (int dr = 0; dr < R; ++dr) {
+    const FileReaction& x = rx[m.order[dr]];
+    double* d = &m.rxd[(size_t)dr * kRxDoubles];
+    d[0] = std::log(x.A);
+    d[1] = x.b;
+    d[2] = x.Ea / kRcal;
+    int* ii = &m.rxi[(size_t)dr * kRxInts];
+    ii[0] = x.reac[0]; ii[1] = x.reac[1]; ii[2] = x.prod[0]; ii[3] = x.prod[1];
+    int nu_of[4] = {0, 0, 0, 0};
+    int uc = 0;
+    for (int s = 0; s < 4; ++s) {
+      int sp = ii[s];
+      if (sp < 0) continue;
+      bool seen = false;
+      for (int u = 0; u < uc; ++u) seen |= (ii[4 + u] == sp);
+      if (!seen) ii[4 + uc++] = sp;
+    }
+    // net coefficients of the distinct slot species
+    for (int u = 0; u < uc; ++u) {
+      int sp = ii[4 + u], nu = 0;
+      for (int s = 0; s < 2; ++s) {
+        if (ii[s] == sp) nu -= 1;
+        if (ii[2 + s] == sp) nu += 1;
+      }
+      nu_of[u] = nu;
+      if (nu != 0) sr[sp].push_back(dr * 8 + (nu + 4));
+    }
+    int nrow = 0;
+    for (int u = 0; u < uc; ++u)
+      if (nu_of[u] != 0 && ii[4 + u] < K - 1) { ii[8 + nrow] = ii[4 + u]; ii[12 + nrow] = nu_of[u]; ++nrow; }
+    for (int s = nrow; s < 4; ++s) ii[12 + s] = 0;
+    m.dnu[dr] = (ii[2] >= 0) + (ii[3] >= 0) - (ii[0] >= 0) - (ii[1] >= 0);
+    if (x.type >= 1) {
+      int pd = dr - m.n_elem;
+      for (int k = 0; k < K; ++k) m.eff[(size_t)pd * K + k] = x.eff[k];
+    }
+    if (x.type >= 2) {
+      int f = dr - m.n_elem - m.n_tb;
+      double* q = &m.fo[(size_t)f * kFoDoubles];
+      q[0] = std::log(x.A0); q[1] = x.b0; q[2] = x.Ea0 / kRcal;
+      q[3] = x.troe[0]; q[4] = x.troe[1]; q[5] = x.troe[2]; q[6] = x.troe[3];
+      q[7] = (x.type == kTroe) ? 1.0 : 0.0;
+    }
+  }
+  m.sr_ptr.assign(K + 1, 0);
+  m.sr_idx.clear();
+  for (int k = 0; k < K; ++k) {
+    m.sr_ptr[k] = (int)m.sr_idx.size();
+    m.sr_idx.insert(m.sr_idx.end(), sr[k].begin(), sr[k].end());
+  }
+  m.sr_ptr[K] = (int)m.sr_idx.size();
+  return true;
+}
+
+}  // namespace chemgpu
