@@ -1,0 +1,293 @@
+"""Benchmark: cells/s per CFD time step for the batched finite-rate chemistry solve.
+
+Workload (one "step"): one chem_integrate call over dt = 1e-5 s for the 256 x 256 (65 536
+cells) shear-layer field of the 53-species / 325-reaction synthetic mechanism at 40 atm,
+rtol 1e-6, atol 1e-10, cold start (every step starts from the same initial field).
+
+Reported: `value` = cells / (device time of the integrate call, CUDA events on the launching
+stream) with the field resident in HBM; `e2e` = the same cells / (H2D copy of the field from
+pinned host memory + the call + D2H copy of the result); `roofline` = achieved FP64 FLOP/s of the
+integrate kernel (algorithmic FLOPs from the oracle's per-step operation count, times the
+kernel's own per-cell step counts) against the FP64 pipe peak; `cpu_baseline` = the CPU oracle
+on a bounded sample of the same field on the host cores.
+
+`--impl reference` times the CPU oracle itself (the reference implementation of this repo's
+method) on a bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cells/s per CFD Δt (53 sp, rtol 1e-6), batched/mixed vs plain FP64; % roofline"
+L2_BYTES = 129 * 2 ** 20
+OPCOUNT_FILE = os.path.join(ROOT, "tests", "golden", "opcount_mech53.json")
+# FLOPs per operation: add, mul and div count 1; an exp or log counts its cost in FMA flops
+# (measured FP64 pipe throughput of exp and log relative to DFMA on GB300: 17 and 31 DFMA)
+FLOP_WEIGHTS = {"add": 1, "mul": 1, "div": 1, "exp": 2 * 17, "log": 2 * 31}
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--cells", type=int, default=0, help="cells per rank (0 = the full 65536-cell field)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0 = auto)")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(w, n_sample: int):
+    """The CPU oracle on a bounded sample of the field, all host cores (threads over cells)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    path = w["mech"].write_temp()
+    ora = oracle.OracleMechanism(path)
+    n = w["T"].shape[0]
+    idx = np.linspace(0, n - 1, n_sample).astype(np.int64)
+    T, Y = w["T"][idx], w["Y"][:, idx]
+    t0 = time.perf_counter()
+    ora.integrate(w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n_sample / dt, "unit": "cells/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_sample} cells evenly spaced over the same 65536-cell field, one integrate each, "
+                      f"{cores} threads (one cell per thread at a time)", "seconds": dt}
+
+
+def run_reference(args, w, world, rank):
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    n_sample = args.cpu_sample or max(cores * 4, 32)
+    for _ in range(args.warmup):
+        cpu_baseline(w, max(cores, 8))
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(w, n_sample))
+    tot_cells = n_sample * args.steps
+    tot_s = sum(v["seconds"] for v in vals)
+    value = tot_cells / tot_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "cells": int(w["T"].shape[0]), "species": 53, "reactions": 325,
+                       "dt_s": w["dt"], "p_atm": 40.0, "rtol": w["rtol"], "atol": w["atol"]},
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores, "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def algorithmic_flops(steps: np.ndarray, rejects: np.ndarray):
+    """FP64 FLOPs the method needs for the given per-cell step counts (oracle operation count per
+    rate evaluation, Jacobian, LU and solve, with the weights above)."""
+    with open(OPCOUNT_FILE) as fh:
+        oc = json.load(fh)
+    per = {k: sum(FLOP_WEIGHTS[o] * v[o] for o in FLOP_WEIGHTS) for k, v in oc["counts"].items()}
+    N = oc["N"]
+    # per attempt: W = I/(gamma h) - J (N^2 + N), LU, 4 stage solves + 1 error-filter solve,
+    # 2 rate evaluations (stages 2 and 3; stage 4 reuses stage 3), stage combinations and error
+    # norm (~ 30 N); per accepted step: one Jacobian (with its own rate evaluation).
+    attempt = N * N + N + per["lu"] + 5 * per["solve"] + 2 * per["rates"] + 30 * N
+    accepted = per["jacobian"]
+    total_steps = int(steps.sum())
+    total_attempts = total_steps + int(rejects.sum())
+    return attempt * total_attempts + accepted * total_steps, {"per_attempt": attempt, "per_accepted": accepted}
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    from paper_2105_12070_gb300 import synth
+    w = synth.workload_shear_layer()
+    if args.impl == "reference":
+        return run_reference(args, w, world, rank)
+
+    import torch
+    from paper_2105_12070_gb300 import chem
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    mech = chem.Mechanism(w["mech"].write_temp())
+    n_total = w["T"].shape[0] if args.cells <= 0 else args.cells
+    # weak scaling: every rank integrates its own copy of the field (cells are independent)
+    idx = np.arange(n_total) % w["T"].shape[0]
+    T_host = torch.from_numpy(w["T"][idx].copy()).pin_memory()
+    Y_host = torch.from_numpy(w["Y"][:, idx].copy()).pin_memory()
+    T_out = torch.empty_like(T_host).pin_memory()
+    Y_out = torch.empty_like(Y_host).pin_memory()
+    T = torch.empty_like(T_host, device="cuda")
+    Y = torch.empty_like(Y_host, device="cuda")
+    status = torch.zeros(n_total, dtype=torch.int32, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    prec = chem.CHEM_PREC_MIXED if args.precision == "mixed" else chem.CHEM_PREC_FP64
+    opts = chem.default_opts(precision=prec)
+    stream = torch.cuda.current_stream()
+
+    def one_step(timed: bool):
+        flush.fill_(1.0)  # L2 flush between steps (outside the events)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        T.copy_(T_host, non_blocking=True)
+        Y.copy_(Y_host, non_blocking=True)
+        e[1].record(stream)
+        chem.chem_integrate(mech, w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], status=status, opts=opts)
+        e[2].record(stream)
+        T_out.copy_(T, non_blocking=True)
+        Y_out.copy_(Y, non_blocking=True)
+        e[3].record(stream)
+        e[3].synchronize()
+        return e[1].elapsed_time(e[2]), e[0].elapsed_time(e[3])
+
+    for _ in range(args.warmup):
+        one_step(False)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    kern_ms, e2e_ms = 0.0, 0.0
+    for _ in range(args.steps):
+        k, e = one_step(True)
+        kern_ms += k
+        e2e_ms += e
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([kern_ms, e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        kern_ms, e2e_ms = t.tolist()
+    st_np = status.cpu().numpy()
+    steps = torch.zeros(n_total, dtype=torch.int32, device="cuda")
+    rej = torch.zeros_like(steps)
+    chem.chem_last_cell_counters(mech, steps, rej)
+    steps_np, rej_np = steps.cpu().numpy(), rej.cpu().numpy()
+    cells = n_total * world * args.steps
+    value = cells / (kern_ms / 1e3)
+    e2e_value = cells / (e2e_ms / 1e3)
+    flops, per = algorithmic_flops(steps_np, rej_np)
+    achieved = flops / (kern_ms / 1e3 / args.steps) / 1e12  # TFLOP/s, one launch
+    peak = fp64_peak_tflops()
+    line = {
+        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": kern_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == chem.CHEM_PREC_FP64 else "f64+f32", "data": "synthetic",
+        "config": {"workload": w["name"], "cells": n_total, "species": 53, "reactions": 325, "dt_s": w["dt"],
+                   "p_atm": 40.0, "rtol": w["rtol"], "atol": w["atol"], "precision": args.precision,
+                   "scheduling": "persistent kernel + device work queue", "l2": "flushed between steps (256 MiB write)",
+                   "start": "cold (every step from the initial field)"},
+        "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": int(T_host.numel() * 8 + Y_host.numel() * 8),
+                "d2h_bytes_per_step": int(T_out.numel() * 8 + Y_out.numel() * 8)},
+        "gpu_launches": 1 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak["tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / peak["tflops"], "traffic": None, "peak_source": peak["source"],
+                     "flops_per_attempt": per["per_attempt"], "flops_per_accepted_step": per["per_accepted"]},
+        "clocks": clk,
+        "cells_status": {str(k): int(v) for k, v in zip(*np.unique(st_np, return_counts=True))},
+        "steps_per_cell": {"mean": float(steps_np.mean()), "max": int(steps_np.max()),
+                           "rejects_mean": float(rej_np.mean())},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample or max(4 * cores, 32))
+        line["cpu_baseline"].pop("seconds", None)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def fp64_peak_tflops():
+    """FP64 FMA pipe peak, measured in this process on this GPU (chem_probe_fp64_peak: 8
+    independent DFMA chains per thread, 4 x 256 threads per SM)."""
+    from paper_2105_12070_gb300 import chem
+    return {"tflops": chem.chem_probe_fp64_peak(), "source": "measured in-process (DFMA microbenchmark)"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

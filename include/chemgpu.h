@@ -58,8 +58,9 @@ typedef struct {
   int max_steps;     /* step attempts per cell per call (default 100000) */
   int use_queue;     /* 1 (default): persistent kernel pulling cells from a device work queue;
                         0: static round-robin assignment of cells to warps */
-  int cells_per_cta; /* warps (cells in flight) per CTA; 0 = automatic */
+  int cells_per_cta; /* cells in flight per CTA; 0 = automatic */
   int ctas_per_sm;   /* resident CTAs per SM for the persistent grid; 0 = automatic */
+  int warps_per_cell; /* 1, 2 or 4 warps cooperate on one cell; 0 = automatic */
 } chem_opts;
 
 typedef struct {
@@ -109,6 +110,12 @@ int chem_integrate(const chem_mech* mech, double p_Pa, double* T, double* Y, int
  * next chem_integrate on the handle. */
 int chem_last_cell_counters(const chem_mech* mech, int32_t* steps, int32_t* rejects, int64_t ncells,
                             void* stream);
+
+/* Diagnostic, not part of the chemistry: measures the FP64 fused-multiply-add throughput of the
+ * current device (8 independent FMA chains per thread, 4 CTAs of 256 threads per SM, ~50 ms)
+ * and returns it in TFLOP/s (2 flops per FMA).  It is the denominator of the roofline that the
+ * benchmark reports for the integrate kernel, measured in the same process and clock state. */
+int chem_probe_fp64_peak(double* tflops);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* chem_last_error(void);

@@ -33,15 +33,20 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, defines=(), out: str | None = None) -> str:
+    """Compiles the library (into `out`, default the in-tree _build/libchemgpu.so); `defines` are
+    extra -D macros (e.g. CHEM_PHASE_TIMERS for the per-phase cycle counters)."""
+    lib = out or LIB
+    if not force and out is None and not _stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir = os.path.dirname(lib)
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE] + ARCH
+    common += [f"-D{d}" for d in defines]
     procs, objs = [], []
     for src in SOURCES:
-        obj = os.path.join(BUILD, src + f".{os.getpid()}.o")
+        obj = os.path.join(build_dir, src + f".{os.getpid()}.o")
         cmd = [nvcc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cpp"):
             cmd[1:1] = ["-x", "cu"]
@@ -58,12 +63,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
             failed.append(src)
     if failed:
         raise RuntimeError("nvcc failed for " + ", ".join(failed))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     subprocess.run([nvcc, "-shared", "-cudart", "static"] + ARCH + ["-o", tmp] + objs, check=True)
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     for o in objs:
         os.remove(o)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

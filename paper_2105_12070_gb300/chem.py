@@ -25,7 +25,8 @@ CELL_STATUS = {0: "ok", 1: "max_steps", 2: "h_underflow", 3: "bad_input"}
 
 class ChemOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("refine_sweeps", ctypes.c_int), ("max_steps", ctypes.c_int),
-                ("use_queue", ctypes.c_int), ("cells_per_cta", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+                ("use_queue", ctypes.c_int), ("cells_per_cta", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("warps_per_cell", ctypes.c_int)]
 
 
 class ChemStats(ctypes.Structure):
@@ -64,8 +65,9 @@ def load_library(build_if_missing: bool = True):
         lib.chem_integrate.argtypes = [vp, dp, vp, vp, i64, dp, dp, dp, vp, vp, ctypes.POINTER(ChemOpts),
                                        ctypes.POINTER(ChemStats), vp]
         lib.chem_last_cell_counters.argtypes = [vp, vp, vp, i64, vp]
+        lib.chem_probe_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double)]
         for name in ("chem_load_mechanism", "chem_mech_dims", "chem_rates", "chem_jacobian", "chem_integrate",
-                     "chem_last_cell_counters"):
+                     "chem_last_cell_counters", "chem_probe_fp64_peak"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -196,3 +198,12 @@ def chem_last_cell_counters(mech: Mechanism, steps, rejects, stream=None):
     ps, dev = _ptr(steps, np.int32)
     pr, _ = _ptr(rejects, np.int32)
     _check(mech._lib.chem_last_cell_counters(mech.handle, ps, pr, n, _stream(stream, dev)))
+
+
+def chem_probe_fp64_peak() -> float:
+    """Measured FP64 FMA throughput of the current device in TFLOP/s (roofline denominator)."""
+    lib = load_library()
+    v = ctypes.c_double()
+    if lib.chem_probe_fp64_peak(ctypes.byref(v)) != 0:
+        raise ChemError(lib.chem_last_error().decode())
+    return v.value

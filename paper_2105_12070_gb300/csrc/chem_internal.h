@@ -7,8 +7,8 @@
 
 namespace chemgpu {
 
-// Reaction kinds in device order: all elementary reactions first, then third-body, then
-// fall-off (Lindemann and Troe), so that lanes of one warp pass mostly run the same branch.
+// Reaction kinds.  Device order: Troe, Lindemann, third-body, elementary, so that lanes of one
+// warp pass mostly run the same branch and the pressure-dependent reactions are 0 .. n_pd-1.
 enum : int { kElementary = 0, kThirdBody = 1, kLindemann = 2, kTroe = 3 };
 
 // Per-reaction integer record (16 ints).
@@ -19,8 +19,8 @@ enum : int { kElementary = 0, kThirdBody = 1, kLindemann = 2, kTroe = 3 };
 constexpr int kRxInts = 16;
 
 // Per-reaction double record.
-//   [0] ln A   [1] b   [2] Ea/Rc (K)
-constexpr int kRxDoubles = 3;
+//   [0] ln A   [1] b   [2] Ea/Rc (K)   [3..6] net coefficients of the rows (as doubles)
+constexpr int kRxDoubles = 7;
 
 // Per fall-off reaction doubles: ln A0, b0, Ea0/Rc, alpha, T3, T1, T2, is_troe
 constexpr int kFoDoubles = 8;
@@ -38,9 +38,25 @@ struct HostMech {
   std::vector<int> dnu;                // [R] products minus reactants
   std::vector<double> eff;             // [n_tb + n_fo][K]
   std::vector<double> fo;              // [n_fo][kFoDoubles]
-  // species -> (reaction, net coefficient) lists, all K species: entry = r * 8 + (nu + 4)
+  // species -> (reaction, net coefficient) lists, all K species
   std::vector<int> sr_ptr;             // [K + 1]
-  std::vector<int> sr_idx;
+  std::vector<int> sr_idx;             // reaction index (device order)
+  std::vector<double> sr_nu;           // net coefficient of the species in that reaction
+  // Jacobian gather plan (mass-action part).  Z entries (row k < K-1 or the enthalpy row K-1,
+  // column j) that receive contributions, each a list of (per-reaction scratch index src,
+  // optional second factor src2 or -1, coefficient): Z[dst] = sum coef * s[src] * s[src2].
+  std::vector<int> zg_ptr;             // [n_entries + 1]
+  std::vector<int> zg_dst;             // [n_entries] row * K + col
+  std::vector<int> zg_src;             // [n_contrib]
+  std::vector<int> zg_src2;            // [n_contrib]
+  std::vector<double> zg_coef;         // [n_contrib]
+  // Efficiency part: for each row (species k < K-1, then the enthalpy row), the
+  // pressure-dependent reactions in it: (pd index, net coefficient; 0 marks the enthalpy row)
+  std::vector<int> pr_ptr;             // [K + 1]
+  std::vector<int> pr_pd;
+  std::vector<double> pr_nu;
+  std::vector<int> pr_row;             // row of each (row, reaction) pair
+  std::vector<int> pr_rows;            // rows with pairs, shortest lists first
 };
 
 // Parse the mechanism text file; false + message on error.
@@ -49,7 +65,7 @@ bool parse_mechanism(const char* path, HostMech& m, std::string& err);
 // Device view of the tables (all pointers into one device allocation).
 struct DevMech {
   int K, R, N;
-  int n_elem, n_tb, n_fo, n_pd;  // n_pd = n_tb + n_fo; PD reactions are indices n_elem .. R-1
+  int n_elem, n_tb, n_fo, n_pd;  // fall-off reactions are 0 .. n_fo-1, pressure-dependent 0 .. n_pd-1
   const double* sp;
   const double* rxd;
   const int* rxi;
@@ -58,6 +74,19 @@ struct DevMech {
   const double* fo;
   const int* sr_ptr;
   const int* sr_idx;
+  const double* sr_nu;
+  int zg_entries;
+  const int* zg_ptr;
+  const int* zg_dst;
+  const int* zg_src;
+  const int* zg_src2;
+  const double* zg_coef;
+  const int* pr_ptr;
+  const int* pr_pd;
+  const double* pr_nu;
+  const int* pr_row;
+  const int* pr_rows;
+  int n_pairs, n_prows;
 };
 
 }  // namespace chemgpu

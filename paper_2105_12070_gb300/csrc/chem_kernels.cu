@@ -28,6 +28,7 @@ namespace {
 
 constexpr double kRu = 8.314462618e7;  // erg/(mol K)
 constexpr double kPatm = 1.01325e6;    // dyn/cm^2
+constexpr double kLnPatmRu = -4.4074185890025275;  // ln(Patm / Ru), Patm/Ru in mol K / cm^3
 constexpr unsigned kFull = 0xffffffffu;
 
 // ------------------------------------------------------------------------------------------
@@ -53,80 +54,182 @@ __constant__ double c_e[4] = {-0.2561963508749719744122, -0.07156405471952786716
                               -0.09930846885424478507654, -0.9949360460805926517866};
 
 // ------------------------------------------------------------------------------------------
-// Per-warp shared-memory plan (doubles unless noted).
+// Cell groups.  G warps (32 G threads) cooperate on one cell; several groups share a CTA and
+// synchronise with their own named barrier (ids 1..15).  Reductions go through a small
+// per-group scratch in a fixed order, so results do not depend on scheduling.
+
+template <int G>
+struct Grp {
+  static constexpr int NT = 32 * G;
+  int t;        // thread index in the group
+  int gid;      // group index in the CTA
+  double* red;  // 6 G doubles of reduction scratch
+  mutable int parity;
+
+  __device__ int lane() const { return t & 31; }
+  __device__ int warp() const { return t >> 5; }
+  __device__ void sync() const {
+    if (G == 1) {
+      __syncwarp();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(NT) : "memory");
+    }
+  }
+  __device__ double sum(double v) const {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (G == 1) return v;
+    double* r = red + (parity & 1) * 3 * G;  // alternate halves: no reader of the previous
+    parity++;                                // call can still be reading this one
+    if (lane() == 0) r[warp()] = v;
+    sync();
+    double s = r[0];
+#pragma unroll
+    for (int i = 1; i < G; ++i) s += r[i];
+    return s;
+  }
+  // two sums at once (one exchange)
+  __device__ void sum2(double& a, double& b) const {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(kFull, a, o);
+      b += __shfl_xor_sync(kFull, b, o);
+    }
+    if (G == 1) return;
+    double* r = red + (parity & 1) * 3 * G;
+    parity++;
+    if (lane() == 0) { r[2 * warp()] = a; r[2 * warp() + 1] = b; }
+    sync();
+    a = r[0];
+    b = r[1];
+#pragma unroll
+    for (int i = 1; i < G; ++i) { a += r[2 * i]; b += r[2 * i + 1]; }
+  }
+  // max that propagates NaN (a NaN error norm must reject the step)
+  __device__ static double nanmax(double a, double b) { return (a > b || a != a) ? a : b; }
+  __device__ double max_nan(double v) const {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(kFull, v, o));
+    if (G == 1) return v;
+    double* r = red + (parity & 1) * 3 * G;
+    parity++;
+    if (lane() == 0) r[warp()] = v;
+    sync();
+    double s = r[0];
+#pragma unroll
+    for (int i = 1; i < G; ++i) s = nanmax(s, r[i]);
+    return s;
+  }
+  // argmax of key (ties to the lowest index) over the group, carrying a value along
+  __device__ void argmax(long long& key, int& idx, double& val) const {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long ok = __shfl_xor_sync(kFull, key, o);
+      const int oi = __shfl_xor_sync(kFull, idx, o);
+      const double ov = __shfl_xor_sync(kFull, val, o);
+      if (ok > key || (ok == key && oi < idx)) { key = ok; idx = oi; val = ov; }
+    }
+    if (G == 1) return;
+    double* r = red + (parity & 1) * 3 * G;
+    parity++;
+    if (lane() == 0) {
+      r[3 * warp()] = __longlong_as_double(key);
+      r[3 * warp() + 1] = __int2double_rn(idx);
+      r[3 * warp() + 2] = val;
+    }
+    sync();
+    key = __double_as_longlong(r[0]);
+    idx = (int)r[1];
+    val = r[2];
+#pragma unroll
+    for (int i = 1; i < G; ++i) {
+      const long long ok = __double_as_longlong(r[3 * i]);
+      const int oi = (int)r[3 * i + 1];
+      if (ok > key || (ok == key && oi < idx)) { key = ok; idx = oi; val = r[3 * i + 2]; }
+    }
+  }
+};
+
+// ------------------------------------------------------------------------------------------
+// Per-cell shared-memory plan (doubles).
 
 struct Plan {
-  int N, K, R, n_pd;
-  int SA;         // size of each of the two matrix buffers: max(N*N, 8*R)
-  int off_A, off_B, off_vec, off_sp, off_q, off_M, off_piv, total;  // in doubles
+  int N, K, R, n_pd, G;
+  int SA;  // size of each of the two matrix buffers: max(N*N, 8*R)
+  int off_A, off_B, off_vec, off_sp, off_q, off_M, off_piv, off_red, total;
 };
 
 __host__ __device__ inline int round2(int x) { return (x + 1) & ~1; }
 
-__host__ __device__ inline Plan make_plan(int K, int R, int n_pd) {
+__host__ __device__ inline Plan make_plan(int K, int R, int n_pd, int G) {
   Plan p;
-  p.N = K; p.K = K; p.R = R; p.n_pd = n_pd;
+  p.N = K; p.K = K; p.R = R; p.n_pd = n_pd; p.G = G;
   p.SA = round2(max(K * K, 8 * R));
   p.off_A = 0;
   p.off_B = p.SA;
   p.off_vec = 2 * p.SA;
-  // vectors: y, ynew, f0, fs, u0..u3, rhs, err, invdiag, zc, dwT, rowA, rowB, ccol  (16 x N)
-  p.off_sp = p.off_vec + 16 * round2(K);
+  // vectors: y, ynew, f0, fs, u0..u3, err, invdiag, rhs, res, (er, ec as ints), (FP32 inverse
+  // pivots)  (14 x N); the Jacobian's temporaries zc, dwT, rowA, rowB, ccol reuse u0..u3, err
+  p.off_sp = p.off_vec + 14 * round2(K);
   // species: C, hRT, cpR, gRT, omega, dcpR  (6 x K)
   p.off_q = p.off_sp + 6 * round2(K);
   p.off_M = p.off_q + round2(R);
   p.off_piv = p.off_M + round2(max(n_pd, 1));
-  p.total = p.off_piv + round2((K + 1) / 2 + 1);
+  p.off_red = p.off_piv + round2(K + 2);  // pivots and the composed permutation (ints)
+  p.total = p.off_red + 6 * G + 2;  // reduction scratch + queue slot
+  p.total = round2(p.total);
   return p;
 }
 
-struct WarpMem {
+struct CellMem {
   double *A, *B;
-  double *y, *ynew, *f0, *fs, *u[4], *rhs, *err, *invdiag, *zc, *dwT, *rowA, *rowB, *ccol;
+  double *y, *ynew, *f0, *fs, *u[4], *err, *invdiag, *zc, *dwT, *rowA, *rowB, *ccol, *rhs, *res;
+  int *er, *ec;
+  float* invd32;
   double *C, *hRT, *cpR, *gRT, *omega, *dcpR;
-  double *q, *M;
+  double *q, *M, *red;
   int* piv;
+  int* perm;
+  int* slot;
 };
 
-__device__ inline WarpMem carve(double* base, const Plan& p) {
-  WarpMem w;
+__device__ inline CellMem carve(double* base, const Plan& p) {
+  CellMem w;
   w.A = base + p.off_A;
   w.B = base + p.off_B;
   const int n = round2(p.K);
   double* v = base + p.off_vec;
   w.y = v; w.ynew = v + n; w.f0 = v + 2 * n; w.fs = v + 3 * n;
   for (int i = 0; i < 4; ++i) w.u[i] = v + (4 + i) * n;
-  w.rhs = v + 8 * n; w.err = v + 9 * n; w.invdiag = v + 10 * n; w.zc = v + 11 * n; w.dwT = v + 12 * n;
-  w.rowA = v + 13 * n; w.rowB = v + 14 * n; w.ccol = v + 15 * n;
+  w.err = v + 8 * n; w.invdiag = v + 9 * n;
+  w.zc = w.u[0]; w.dwT = w.u[1]; w.rowA = w.u[2]; w.rowB = w.u[3]; w.ccol = w.err;
+  w.rhs = v + 10 * n; w.res = v + 11 * n;
+  w.er = reinterpret_cast<int*>(v + 12 * n);
+  w.ec = w.er + n;
+  w.invd32 = reinterpret_cast<float*>(v + 13 * n);
   double* s = base + p.off_sp;
   w.C = s; w.hRT = s + n; w.cpR = s + 2 * n; w.gRT = s + 3 * n; w.omega = s + 4 * n; w.dcpR = s + 5 * n;
   w.q = base + p.off_q;
   w.M = base + p.off_M;
   w.piv = reinterpret_cast<int*>(base + p.off_piv);
+  w.perm = w.piv + p.K + 2;
+  w.red = base + p.off_red;
+  w.slot = reinterpret_cast<int*>(base + p.off_red + 6 * p.G);
   return w;
 }
 
-__device__ inline double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-
-// max that propagates NaN (a NaN error norm must reject the step)
-__device__ inline double nanmax(double a, double b) { return (a > b || a != a) ? a : b; }
-
-__device__ inline double warp_max_nan(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(kFull, v, o));
-  return v;
-}
-
 // ------------------------------------------------------------------------------------------
-// Thermochemistry and rates (Eq. 1).  Scalars of the cell state, identical in every lane.
+// Thermochemistry and rates (Eq. 1).  Scalars of the cell state, identical in every thread.
 
 struct CellScalars {
-  double T, invT, lnT, rho, Wbar, cp, dcp_dT, fT, Q;
+  double T, invT, lnT, rho, inv_rho, Wbar, cp, dcp_dT, fT;
 };
+
+// 2^k as a double (|k| < 1000), exact.
+__device__ inline double pow2(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
+
+// Binary exponent of |a| (the biased exponent field; 0 for zero and subnormals).
+__device__ inline int exp_field(double a) { return (int)((__double_as_longlong(a) >> 52) & 0x7ff); }
 
 // NASA-7: cp/R, h/RT, s/R and d(cp/R)/dT.
 __device__ inline void nasa7(const double* a, double T, double invT, double lnT, double& cpR, double& hRT,
@@ -165,9 +268,10 @@ __device__ inline void troe(const double* fo, double T, double invT, double Pr, 
 // scr[r*8 + 0..7] = {dq/dC at the 4 distinct slot species, phi (coefficient of the
 // efficiencies), sum_j dq/dC_j C_j, dq/dT at fixed C, reaction enthalpy (erg/mol)} and the
 // species production rates in w.omega.
-__device__ CellScalars warp_rates(const DevMech& m, double p, const double* y, double* f, const WarpMem& w,
-                                  double* scr, bool jac) {
-  const int lane = threadIdx.x & 31;
+template <int G>
+__device__ CellScalars cell_rates(const DevMech& m, const Grp<G>& g, double p, const double* y, double* f,
+                                  const CellMem& w, double* scr, bool jac) {
+  constexpr int NT = Grp<G>::NT;
   const int K = m.K, d = K - 1;
   CellScalars s;
   s.T = y[0];
@@ -175,19 +279,19 @@ __device__ CellScalars warp_rates(const DevMech& m, double p, const double* y, d
   s.lnT = log(s.T);
   // mass fractions, mean molar mass, density, concentrations, thermo
   double ysum = 0.0, yw = 0.0;
-  for (int k = lane; k < d; k += 32) {
+  for (int k = g.t; k < d; k += NT) {
     const double Yk = y[1 + k];
     ysum += Yk;
     yw += Yk * m.sp[k * kSpDoubles + 1];
   }
-  ysum = warp_sum(ysum);
-  yw = warp_sum(yw);
+  g.sum2(ysum, yw);
   const double Yd = 1.0 - ysum;
   yw += Yd * m.sp[d * kSpDoubles + 1];
   s.Wbar = 1.0 / yw;
   s.rho = p * s.Wbar / (kRu * s.T);
+  s.inv_rho = yw * kRu * s.T / p;
   double cp = 0.0, dcp = 0.0;
-  for (int k = lane; k < K; k += 32) {
+  for (int k = g.t; k < K; k += NT) {
     const double* sp = m.sp + k * kSpDoubles;
     const double Yk = (k < d) ? y[1 + k] : Yd;
     w.C[k] = s.rho * Yk * sp[1];
@@ -201,26 +305,32 @@ __device__ CellScalars warp_rates(const DevMech& m, double p, const double* y, d
     cp += Yk * cpR * sp[1];
     dcp += Yk * dcpR * sp[1];
   }
-  s.cp = warp_sum(cp) * kRu;
-  s.dcp_dT = warp_sum(dcp) * kRu;
-  __syncwarp();
-  // third-body concentrations [M]_r = sum_k eff_rk C_k for the pressure-dependent reactions
-  for (int r = lane; r < m.n_pd; r += 32) {
+  g.sum2(cp, dcp);
+  s.cp = cp * kRu;
+  s.dcp_dT = dcp * kRu;
+  g.sync();
+  // third-body concentrations [M]_r = sum_k eff_rk C_k of the pressure-dependent reactions
+  for (int r = g.t; r < m.n_pd; r += NT) {
     const double* e = m.eff + (size_t)r * K;
-    double acc = 0.0;
-    for (int k = 0; k < K; ++k) acc += e[k] * w.C[k];
-    w.M[r] = acc;
+    double a0 = 0.0, a1 = 0.0;
+    int k = 0;
+    for (; k + 1 < K; k += 2) {
+      a0 = fma(e[k], w.C[k], a0);
+      a1 = fma(e[k + 1], w.C[k + 1], a1);
+    }
+    if (k < K) a0 = fma(e[k], w.C[k], a0);
+    w.M[r] = a0 + a1;
   }
-  __syncwarp();
-  const double ln_patm_rut = log(kPatm / (kRu * s.T));
-  for (int r = lane; r < m.R; r += 32) {
+  g.sync();
+  const double ln_patm_rut = kLnPatmRu - s.lnT;  // ln(Patm / (Ru T))
+  for (int r = g.t; r < m.R; r += NT) {
     const int* ii = m.rxi + r * kRxInts;
     const double* rd = m.rxd + r * kRxDoubles;
     const int a0 = ii[0], a1 = ii[1], p0 = ii[2], p1 = ii[3];
     const double Ca0 = w.C[a0], Ca1 = (a1 >= 0) ? w.C[a1] : 1.0;
     const double Cp0 = w.C[p0], Cp1 = (p1 >= 0) ? w.C[p1] : 1.0;
     const double pf = Ca0 * Ca1, pr = Cp0 * Cp1;
-    double kf = exp(rd[0] + rd[1] * s.lnT - rd[2] * s.invT);
+    double kf = exp(fma(rd[1], s.lnT, rd[0]) - rd[2] * s.invT);
     double dG = w.gRT[p0] - w.gRT[a0];
     if (p1 >= 0) dG += w.gRT[p1];
     if (a1 >= 0) dG -= w.gRT[a1];
@@ -229,13 +339,13 @@ __device__ CellScalars warp_rates(const DevMech& m, double p, const double* y, d
     const double invKc = exp(dG - dnu * ln_patm_rut);
     double mfac = 1.0, Mr = 0.0;
     double Pr = 0.0, F = 1.0, dlF = 0.0, dlnF_dT = 0.0, k0 = 0.0;
-    const bool pd = r >= m.n_elem;
-    const bool fo = r >= m.n_elem + m.n_tb;
+    const bool pd = r < m.n_pd;
+    const bool fo = r < m.n_fo;
     const double* fop = nullptr;
-    if (pd) Mr = w.M[r - m.n_elem];
+    if (pd) Mr = w.M[r];
     if (fo) {
-      fop = m.fo + (size_t)(r - m.n_elem - m.n_tb) * kFoDoubles;
-      k0 = exp(fop[0] + fop[1] * s.lnT - fop[2] * s.invT);
+      fop = m.fo + (size_t)r * kFoDoubles;
+      k0 = exp(fma(fop[1], s.lnT, fop[0]) - fop[2] * s.invT);
       Pr = k0 * Mr / kf;
       if (fop[7] != 0.0) troe(fop, s.T, s.invT, Pr, F, dlF, dlnF_dT, jac);
       kf = kf * Pr / (1.0 + Pr) * F;
@@ -251,18 +361,20 @@ __device__ CellScalars warp_rates(const DevMech& m, double p, const double* y, d
       if (p1 >= 0) dH += w.hRT[p1];
       if (a1 >= 0) dH -= w.hRT[a1];
       const double dlnKc_dT = (dH - dnu) * s.invT;
-      const double dlnkinf = rd[1] * s.invT + rd[2] * s.invT * s.invT;
+      const double dlnkinf = (rd[1] + rd[2] * s.invT) * s.invT;
       double phi = 0.0, dlnk = dlnkinf;
       if (fo) {
-        const double dk_dM = k0 * F / (1.0 + Pr) * (1.0 / (1.0 + Pr) + dlF);
+        const double inv1p = 1.0 / (1.0 + Pr);
+        const double dk_dM = k0 * F * inv1p * (inv1p + dlF);
         phi = dk_dM * (pf - invKc * pr);
-        const double dlnk0 = fop[1] * s.invT + fop[2] * s.invT * s.invT;
-        dlnk = dlnkinf + (1.0 / (1.0 + Pr) + dlF) * (dlnk0 - dlnkinf) + dlnF_dT;
+        const double dlnk0 = (fop[1] + fop[2] * s.invT) * s.invT;
+        dlnk = dlnkinf + (inv1p + dlF) * (dlnk0 - dlnkinf) + dlnF_dT;
       } else if (pd) {
         phi = kf * pf - kr * pr;
       }
       const double dqdT = mfac * (kf * dlnk * pf - kr * (dlnk - dlnKc_dT) * pr);
       double DC = phi * Mr;
+#pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int j = ii[4 + u];
         double D = 0.0;
@@ -270,7 +382,7 @@ __device__ CellScalars warp_rates(const DevMech& m, double p, const double* y, d
           const double dpf = (a0 == j ? Ca1 : 0.0) + (a1 == j ? Ca0 : 0.0);
           const double dpr = (p0 == j ? Cp1 : 0.0) + (p1 == j ? Cp0 : 0.0);
           D = mfac * (kf * dpf - kr * dpr);
-          DC += D * w.C[j];
+          DC = fma(D, w.C[j], DC);
         }
         o[u] = D;
       }
@@ -280,132 +392,129 @@ __device__ CellScalars warp_rates(const DevMech& m, double p, const double* y, d
       o[7] = dH * kRu * s.T;
     }
   }
-  __syncwarp();
+  g.sync();
   // species production rates and the source term
   double Qp = 0.0;
-  for (int k = lane; k < K; k += 32) {
+  for (int k = g.t; k < K; k += NT) {
     double om = 0.0;
-    for (int e = m.sr_ptr[k]; e < m.sr_ptr[k + 1]; ++e) {
-      const int code = m.sr_idx[e];
-      om += (double)((code & 7) - 4) * w.q[code >> 3];
-    }
+    for (int e = m.sr_ptr[k]; e < m.sr_ptr[k + 1]; ++e) om = fma(m.sr_nu[e], w.q[m.sr_idx[e]], om);
     w.omega[k] = om;
-    Qp += w.hRT[k] * om;
-    if (k < d) f[1 + k] = m.sp[k * kSpDoubles] * om / s.rho;
+    Qp = fma(w.hRT[k], om, Qp);
+    if (k < d) f[1 + k] = m.sp[k * kSpDoubles] * om * s.inv_rho;
   }
-  s.Q = warp_sum(Qp) * kRu * s.T;
-  s.fT = -s.Q / (s.rho * s.cp);
-  if (lane == 0) f[0] = s.fT;
-  __syncwarp();
+  const double Q = g.sum(Qp) * kRu * s.T;
+  s.fT = -Q * s.inv_rho / s.cp;
+  if (g.t == 0) f[0] = s.fT;
+  g.sync();
   return s;
 }
 
-// Assemble the analytical Jacobian (Sec. 2.3) at the state of the preceding warp_rates(jac)
-// call.  scr (= the J buffer, overwritten) holds the per-reaction data, Z is scratch (N*N),
-// J receives d f / d phi.  Chain rule through C_j = rho Y_j / W_j, rho = p Wbar/(Ru T),
-// Y_K = 1 - sum Y_i; Z rows k < K-1 hold d omega_k / dC, row K-1 holds d Q / dC.
-__device__ void warp_jacobian(const DevMech& m, const CellScalars& s, const double* f, const WarpMem& w, double* J,
-                              double* Z) {
-  const int lane = threadIdx.x & 31;
+// Assemble the analytical Jacobian (Sec. 2.3) at the state of the preceding cell_rates(jac)
+// call.  J (overwritten) holds the per-reaction data on entry, Z is N*N scratch, J receives
+// d f / d phi.  Chain rule through C_j = rho Y_j / W_j, rho = p Wbar/(Ru T), Y_K = 1 - sum Y_i;
+// Z rows k < K-1 hold d omega_k / dC, row K-1 holds d Q / dC (Q = sum_k H_k omega_k).
+template <int G>
+__device__ void cell_jacobian(const DevMech& m, const Grp<G>& g, const CellScalars& s, const double* f,
+                              const CellMem& w, double* J, double* Z) {
+  constexpr int NT = Grp<G>::NT;
   const int K = m.K, N = K, d = K - 1;
   const double* scr = J;
-  for (int e = lane; e < N * N; e += 32) Z[e] = 0.0;
-  __syncwarp();
-  // mass-action part: each reaction touches at most 4 rows (+ the Q row) x 4 columns
-  for (int r = 0; r < m.R; ++r) {
-    if (lane < 20) {
-      const int* ii = m.rxi + r * kRxInts;
-      const int rs = lane >> 2, cs = lane & 3;
-      const int col = ii[4 + cs];
-      if (col >= 0) {
-        const double D = scr[(size_t)r * 8 + cs];
-        if (rs < 4) {
-          const int row = ii[8 + rs];
-          if (row >= 0) Z[row * N + col] += (double)ii[12 + rs] * D;
-        } else {
-          Z[d * N + col] += scr[(size_t)r * 8 + 7] * D;
-        }
-      }
+  for (int e = g.t; e < N * N; e += NT) Z[e] = 0.0;
+  g.sync();
+  // mass-action part: one thread per receiving Z entry sums its contributions (a fixed plan
+  // built with the mechanism; no two threads write the same entry, no atomics)
+  for (int e = g.t; e < m.zg_entries; e += NT) {
+    double acc = 0.0;
+    const int cb = m.zg_ptr[e], ce = m.zg_ptr[e + 1];
+    for (int c = cb; c < ce; ++c) {
+      double v = scr[m.zg_src[c]];
+      const int s2 = m.zg_src2[c];
+      if (s2 >= 0) v *= scr[s2];
+      acc = fma(m.zg_coef[c], v, acc);
     }
-    __syncwarp();
+    Z[m.zg_dst[e]] = acc;
   }
-  // efficiency part of the pressure-dependent reactions: rows x all columns
-  for (int r = m.n_elem; r < m.R; ++r) {
-    const int* ii = m.rxi + r * kRxInts;
+  g.sync();
+  // efficiency part of the pressure-dependent reactions: Z[k][j] += sum_r v_kr eff_rj over the
+  // (row k, reaction r) pairs, v_kr = nu_kr phi_r (row K-1, the enthalpy row: dH_r phi_r).
+  // The coefficients go to the stage-vector area first (free while the Jacobian is built).
+  double* v = w.u[0];
+  for (int c = g.t; c < m.n_pairs; c += NT) {
+    const int r = m.pr_pd[c];
     const double phi = scr[(size_t)r * 8 + 4];
-    const double* e = m.eff + (size_t)(r - m.n_elem) * K;
-    for (int rs = 0; rs < 5; ++rs) {
-      int row;
-      double coef;
-      if (rs < 4) {
-        row = ii[8 + rs];
-        if (row < 0) continue;
-        coef = (double)ii[12 + rs] * phi;
-      } else {
-        row = d;
-        coef = scr[(size_t)r * 8 + 7] * phi;
-      }
-      for (int j = lane; j < K; j += 32) Z[row * N + j] += coef * e[j];
-    }
-    __syncwarp();
+    v[c] = (m.pr_row[c] < d) ? m.pr_nu[c] * phi : scr[(size_t)r * 8 + 7] * phi;
   }
+  g.sync();
+  {
+    const float invK = 1.0f / (float)K;
+    const int items = m.n_prows * K;
+    for (int x = g.t; x < items; x += NT) {
+      const int ri = (int)(((float)x + 0.5f) * invK), j = x - ri * K;
+      const int row = m.pr_rows[ri];
+      double acc = 0.0;
+      for (int c = m.pr_ptr[row]; c < m.pr_ptr[row + 1]; ++c) acc = fma(v[c], m.eff[(size_t)m.pr_pd[c] * K + j], acc);
+      Z[row * N + j] += acc;
+    }
+  }
+  g.sync();
   // per-species gathers of sum_j dq/dC_j C_j and dq/dT
-  for (int k = lane; k < d; k += 32) {
+  for (int k = g.t; k < d; k += NT) {
     double zc = 0.0, dw = 0.0;
     for (int e = m.sr_ptr[k]; e < m.sr_ptr[k + 1]; ++e) {
-      const int code = m.sr_idx[e];
-      const double nu = (double)((code & 7) - 4);
-      const int r = code >> 3;
-      zc += nu * scr[(size_t)r * 8 + 5];
-      dw += nu * scr[(size_t)r * 8 + 6];
+      const double nu = m.sr_nu[e];
+      const int r = m.sr_idx[e];
+      zc = fma(nu, scr[(size_t)r * 8 + 5], zc);
+      dw = fma(nu, scr[(size_t)r * 8 + 6], dw);
     }
     w.zc[k] = zc;
     w.dwT[k] = dw;
   }
   double zqc = 0.0, dqt = 0.0;
-  for (int r = lane; r < m.R; r += 32) {
+  for (int r = g.t; r < m.R; r += NT) {
     const double dh = scr[(size_t)r * 8 + 7];
-    zqc += dh * scr[(size_t)r * 8 + 5];
-    dqt += dh * scr[(size_t)r * 8 + 6];
+    zqc = fma(dh, scr[(size_t)r * 8 + 5], zqc);
+    dqt = fma(dh, scr[(size_t)r * 8 + 6], dqt);
   }
-  zqc = warp_sum(zqc);
-  dqt = warp_sum(dqt);
+  zqc = g.sum(zqc);
+  dqt = g.sum(dqt);
   double cpw = 0.0;
-  for (int k = lane; k < K; k += 32) cpw += w.cpR[k] * w.omega[k];
-  cpw = warp_sum(cpw) * kRu;
-  __syncwarp();
+  for (int k = g.t; k < K; k += NT) cpw = fma(w.cpR[k], w.omega[k], cpw);
+  cpw = g.sum(cpw) * kRu;
+  g.sync();
   // per-row and per-column factors
   const double invWd = m.sp[d * kSpDoubles + 1];
-  for (int k = lane; k < d; k += 32) {
+  for (int k = g.t; k < d; k += NT) {
     const double Wk = m.sp[k * kSpDoubles];
     w.rowA[k] = Wk * invWd * Z[k * N + d];
-    w.rowB[k] = Wk / s.rho * (w.zc[k] - w.omega[k]);
+    w.rowB[k] = Wk * s.inv_rho * (w.zc[k] - w.omega[k]);
     w.ccol[k] = -s.Wbar * (m.sp[k * kSpDoubles + 1] - invWd);
   }
-  __syncwarp();
-  const double rhocp = s.rho * s.cp;
+  g.sync();
+  const double inv_rhocp = s.inv_rho / s.cp;
+  const double inv_cp = 1.0 / s.cp;
   const double fT = s.fT;
   // temperature row and column, then the species block (J now overwrites the scratch)
   const double ZQd = Z[d * N + d];
   const double cpd = w.cpR[d] * invWd;
-  for (int i = lane; i < d; i += 32) {
+  for (int i = g.t; i < d; i += NT) {
     const double ci = w.ccol[i];
     const double invWi = m.sp[i * kSpDoubles + 1];
-    const double dQdY = s.rho * invWi * Z[d * N + i] - s.rho * invWd * ZQd + zqc * ci;
+    const double dQdY = s.rho * (invWi * Z[d * N + i] - invWd * ZQd) + zqc * ci;
     const double dcpdY = (w.cpR[i] * invWi - cpd) * kRu;
-    J[1 + i] = -dQdY / rhocp - fT * (ci + dcpdY / s.cp);
+    J[1 + i] = -dQdY * inv_rhocp - fT * (ci + dcpdY * inv_cp);
     const double Wk = m.sp[i * kSpDoubles];
-    J[(1 + i) * N] = Wk / s.rho * (w.dwT[i] - w.zc[i] * s.invT) + f[1 + i] * s.invT;
+    J[(1 + i) * N] = Wk * s.inv_rho * (w.dwT[i] - w.zc[i] * s.invT) + f[1 + i] * s.invT;
   }
-  if (lane == 0) J[0] = -(cpw + dqt - zqc * s.invT) / rhocp - fT * (-s.invT + s.dcp_dT / s.cp);
+  if (g.t == 0) J[0] = -(cpw + dqt - zqc * s.invT) * inv_rhocp - fT * (-s.invT + s.dcp_dT * inv_cp);
   const int nb = d * d;
-  for (int e = lane; e < nb; e += 32) {
-    const int k = e / d, i = e - k * d;
+  const float inv_d = 1.0f / (float)d;
+  for (int e = g.t; e < nb; e += NT) {
+    const int k = (int)(((float)e + 0.5f) * inv_d), i = e - k * d;
     const double Wk = m.sp[k * kSpDoubles];
     const double invWi = m.sp[i * kSpDoubles + 1];
     J[(1 + k) * N + 1 + i] = fma(w.rowB[k], w.ccol[i], fma(Wk * invWi, Z[k * N + i], -w.rowA[k]));
   }
-  __syncwarp();
+  g.sync();
 }
 
 // ------------------------------------------------------------------------------------------
@@ -413,76 +522,215 @@ __device__ void warp_jacobian(const DevMech& m, const CellScalars& s, const doub
 // substitutions that use it (Sec. 2.3: dense LU + back substitution).  Returns false on an
 // exactly zero pivot.
 
-__device__ bool warp_lu(double* A, int N, int* piv, double* invdiag) {
-  const int lane = threadIdx.x & 31;
+// |a| as an ordered integer key (bit pattern of a non-negative float / double)
+__device__ inline long long abs_key(double a) { return __double_as_longlong(fabs(a)); }
+__device__ inline long long abs_key(float a) { return (long long)__float_as_int(fabsf(a)); }
+
+template <int G, typename S>
+__device__ bool cell_lu(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* invdiag) {
+  constexpr int NT = Grp<G>::NT;
   bool ok = true;
   for (int k = 0; k < N; ++k) {
     // pivot: largest |a_ik|, compared as the bit patterns of |a| (monotone for non-negative)
     long long best = -1;
     int bi = N;
-    for (int i = k + lane; i < N; i += 32) {
-      const long long v = __double_as_longlong(fabs(A[i * N + k]));
-      if (v > best) { best = v; bi = i; }
+    double bv = 0.0;
+    for (int i = k + g.t; i < N; i += NT) {
+      const S a = A[i * N + k];
+      const long long v = abs_key(a);
+      if (v > best) { best = v; bi = i; bv = (double)a; }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const long long ob = __shfl_xor_sync(kFull, best, o);
-      const int oi = __shfl_xor_sync(kFull, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    g.argmax(best, bi, bv);
+    // one thread takes the reciprocal of the pivot while the others swap the rows
+    if (g.t == 0) {
+      piv[k] = bi;
+      invdiag[k] = S(1) / S(bv);
     }
-    if (lane == 0) piv[k] = bi;
-    if (best <= 0) ok = false;  // zero (or all-zero) column: singular
+    if (best <= 0) ok = false;  // zero column: singular
     if (bi != k) {
-      for (int j = lane; j < N; j += 32) {
-        const double t = A[k * N + j];
+      for (int j = g.t; j < N; j += NT) {
+        const S t = A[k * N + j];
         A[k * N + j] = A[bi * N + j];
         A[bi * N + j] = t;
       }
     }
-    __syncwarp();
-    const double inv = 1.0 / A[k * N + k];
-    if (lane == 0) invdiag[k] = inv;
-    for (int i = k + 1 + lane; i < N; i += 32) A[i * N + k] *= inv;
-    __syncwarp();
+    g.sync();
+    const S inv = invdiag[k];
+    for (int i = k + 1 + g.t; i < N; i += NT) A[i * N + k] *= inv;
+    g.sync();
     const int mm = N - k - 1;
     const int tot = mm * mm;
     if (tot > 0) {
-      int ei = lane / mm, ej = lane - (lane / mm) * mm;
-      for (int e = lane; e < tot; e += 32) {
-        const int i = k + 1 + ei, j = k + 1 + ej;
-        A[i * N + j] = fma(-A[i * N + k], A[k * N + j], A[i * N + j]);
-        ej += 32;
-        while (ej >= mm) { ej -= mm; ++ei; }
+      const float inv_m = 1.0f / (float)mm;
+      S* Ak = A + (size_t)(k + 1) * N + k;  // column k of the trailing rows
+      const S* U = A + (size_t)k * N + k + 1;  // pivot row right of the diagonal
+      S* T0 = A + (size_t)(k + 1) * N + k + 1;
+      // four independent updates per thread and iteration (loads first, then the FMAs)
+      int e = g.t;
+      for (; e + 3 * NT < tot; e += 4 * NT) {
+        int ii[4], jj[4];
+        S l[4], u[4], a[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int x = e + q * NT;
+          ii[q] = (int)(((float)x + 0.5f) * inv_m);
+          jj[q] = x - ii[q] * mm;
+          l[q] = Ak[ii[q] * N];
+          u[q] = U[jj[q]];
+          a[q] = T0[ii[q] * N + jj[q]];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) T0[ii[q] * N + jj[q]] = fma(-l[q], u[q], a[q]);
+      }
+      for (; e < tot; e += NT) {
+        const int i = (int)(((float)e + 0.5f) * inv_m);
+        const int j = e - i * mm;
+        T0[i * N + j] = fma(-Ak[i * N], U[j], T0[i * N + j]);
       }
     }
-    __syncwarp();
+    g.sync();
   }
+  // compose the row interchanges: row i of the factors is row perm[i] of the original matrix
+  if (g.t == 0) {
+    for (int i = 0; i < N; ++i) perm[i] = i;
+    for (int k = 0; k < N; ++k) {
+      const int p = piv[k];
+      const int t = perm[k];
+      perm[k] = perm[p];
+      perm[p] = t;
+    }
+  }
+  g.sync();
   return ok;
 }
 
-// x <- A^-1 x with the factors of warp_lu.
-__device__ void warp_lu_solve(const double* A, int N, const int* piv, const double* invdiag, double* x) {
+// x <- A^-1 x with the factors of cell_lu, by one warp with x in registers: lane l holds rows
+// l, l+32, l+64, l+96 (N <= 128), so a column step is a shuffle and at most 4 FMAs, without
+// shared-memory round trips or barriers.  perm is the composed row permutation of the LU.
+__device__ void warp_lu_solve(const double* A, int N, const int* perm, const double* invdiag, double* x) {
   const int lane = threadIdx.x & 31;
-  if (lane == 0) {
-    for (int k = 0; k < N; ++k) {
-      const int p = piv[k];
-      if (p != k) { const double t = x[k]; x[k] = x[p]; x[p] = t; }
-    }
+  double xr[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int i = lane + 32 * s;
+    xr[s] = (i < N) ? x[perm[i]] : 0.0;
   }
   __syncwarp();
+  // forward substitution with the unit lower factor
   for (int j = 0; j < N - 1; ++j) {
-    const double xj = x[j];
-    for (int i = j + 1 + lane; i < N; i += 32) x[i] = fma(-A[i * N + j], xj, x[i]);
-    __syncwarp();
+    const int js = j >> 5, jl = j & 31;
+    const double src = js == 0 ? xr[0] : js == 1 ? xr[1] : js == 2 ? xr[2] : xr[3];
+    const double xj = __shfl_sync(kFull, src, jl);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      if (32 * s + 31 > j && 32 * s < N) {  // slot holds rows below j (warp-uniform test)
+        const int i = lane + 32 * s;
+        if (i > j && i < N) xr[s] = fma(-A[i * N + j], xj, xr[s]);
+      }
+    }
+  }
+  // back substitution with the upper factor
+  for (int j = N - 1; j >= 0; --j) {
+    const int js = j >> 5, jl = j & 31;
+    const double src = js == 0 ? xr[0] : js == 1 ? xr[1] : js == 2 ? xr[2] : xr[3];
+    const double xj = __shfl_sync(kFull, src, jl) * invdiag[j];
+    if (lane == jl) {
+      if (js == 0) xr[0] = xj; else if (js == 1) xr[1] = xj; else if (js == 2) xr[2] = xj; else xr[3] = xj;
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      if (32 * s < j) {  // slot holds rows above j (warp-uniform test)
+        const int i = lane + 32 * s;
+        if (i < j) xr[s] = fma(-A[i * N + j], xj, xr[s]);
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int i = lane + 32 * s;
+    if (i < N) x[i] = xr[s];
+  }
+  __syncwarp();
+}
+
+// Mixed precision: x <- W^-1 b through the FP32 factors of the equilibrated matrix
+// S = D_r W D_c (D_r, D_c powers of two): z = D_r b, S v = z in FP32, x = D_c v.  One warp,
+// v in registers as in warp_lu_solve.
+__device__ void warp_lu_solve32(const float* A, int N, const int* perm, const float* invdiag, const int* er,
+                                const int* ec, const double* b, double* x) {
+  const int lane = threadIdx.x & 31;
+  float xr[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int i = lane + 32 * s;
+    if (i < N) {
+      const int pi = perm[i];
+      xr[s] = (float)(b[pi] * pow2(-er[pi]));
+    } else {
+      xr[s] = 0.0f;
+    }
+  }
+  for (int j = 0; j < N - 1; ++j) {
+    const int js = j >> 5, jl = j & 31;
+    const float src = js == 0 ? xr[0] : js == 1 ? xr[1] : js == 2 ? xr[2] : xr[3];
+    const float xj = __shfl_sync(kFull, src, jl);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      if (32 * s + 31 > j && 32 * s < N) {
+        const int i = lane + 32 * s;
+        if (i > j && i < N) xr[s] = fmaf(-A[i * N + j], xj, xr[s]);
+      }
+    }
   }
   for (int j = N - 1; j >= 0; --j) {
-    const double xj = x[j] * invdiag[j];
-    __syncwarp();
-    if (lane == 0) x[j] = xj;
-    for (int i = lane; i < j; i += 32) x[i] = fma(-A[i * N + j], xj, x[i]);
-    __syncwarp();
+    const int js = j >> 5, jl = j & 31;
+    const float src = js == 0 ? xr[0] : js == 1 ? xr[1] : js == 2 ? xr[2] : xr[3];
+    const float xj = __shfl_sync(kFull, src, jl) * invdiag[j];
+    if (lane == jl) {
+      if (js == 0) xr[0] = xj; else if (js == 1) xr[1] = xj; else if (js == 2) xr[2] = xj; else xr[3] = xj;
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      if (32 * s < j) {
+        const int i = lane + 32 * s;
+        if (i < j) xr[s] = fmaf(-A[i * N + j], xj, xr[s]);
+      }
+    }
   }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int i = lane + 32 * s;
+    if (i < N) x[i] = (double)xr[s] * pow2(-ec[i]);
+  }
+  __syncwarp();
 }
+
+template <int G>
+__device__ inline void cell_solve(const Grp<G>& g, const double* A, int N, const int* perm, const double* invdiag,
+                                  double* x) {
+  if (g.warp() == 0) warp_lu_solve(A, N, perm, invdiag, x);
+  g.sync();
+}
+
+// ------------------------------------------------------------------------------------------
+// Optional per-phase cycle counters (compile with -DCHEM_PHASE_TIMERS): thread 0 of each cell
+// group accumulates clock64() deltas per phase; read with chem_debug_phase_cycles().
+
+#ifdef CHEM_PHASE_TIMERS
+__device__ unsigned long long g_phase_cycles[8];
+#define PHASE_BEGIN long long ph_t0_ = clock64();
+#define PHASE_END(slot)                                                  \
+  do {                                                                    \
+    long long ph_t1_ = clock64();                                         \
+    if (g.t == 0) atomicAdd(&g_phase_cycles[slot], (unsigned long long)(ph_t1_ - ph_t0_)); \
+    ph_t0_ = ph_t1_;                                                      \
+  } while (0)
+#else
+#define PHASE_BEGIN
+#define PHASE_END(slot) \
+  do {                  \
+  } while (0)
+#endif
 
 // ------------------------------------------------------------------------------------------
 // Kernels
@@ -499,112 +747,247 @@ struct IntegrateArgs {
   int64_t ncells;
   int max_steps;
   int use_queue;
+  int mixed;          // FP32 factors + FP64-residual refinement
+  int refine_sweeps;  // refinement sweeps per stage solve (mixed)
 };
 
-__device__ inline int64_t next_cell(const IntegrateArgs& a, int64_t& static_next, int64_t stride) {
+// ------------------------------------------------------------------------------------------
+// Mixed precision (FP32 LU + FP64-residual iterative refinement).
+
+// Equilibrate W = I gh - J by powers of two (row exponents er, then column exponents ec, from
+// the largest entries) and factor S = D_r W D_c in FP32 in the first half of buffer B.
+template <int G>
+__device__ bool form_and_factor32(const Grp<G>& g, const CellMem& w, int N, double gh) {
+  constexpr int NT = Grp<G>::NT;
+  float* S = reinterpret_cast<float*>(w.B);
+  for (int i = g.t; i < N; i += NT) {
+    int mx = 0;
+    for (int j = 0; j < N; ++j) {
+      const double v = (i == j) ? gh - w.A[i * N + j] : w.A[i * N + j];
+      mx = max(mx, exp_field(v));
+    }
+    w.er[i] = mx - 1023;
+  }
+  g.sync();
+  for (int j = g.t; j < N; j += NT) {
+    int mx = -2100;
+    for (int i = 0; i < N; ++i) {
+      const double v = (i == j) ? gh - w.A[i * N + j] : w.A[i * N + j];
+      const int ef = exp_field(v);
+      if (ef > 0) mx = max(mx, ef - 1023 - w.er[i]);
+    }
+    w.ec[j] = (mx < -900) ? 0 : mx;
+  }
+  g.sync();
+  for (int e = g.t; e < N * N; e += NT) {
+    const int i = e / N, j = e - (e / N) * N;
+    const double v = (i == j) ? gh - w.A[e] : -w.A[e];
+    S[e] = (float)(v * pow2(-w.er[i] - w.ec[j]));
+  }
+  g.sync();
+  return cell_lu<G, float>(g, S, N, w.piv, w.perm, w.invd32);
+}
+
+// u <- W^-1 rhs.  FP64 factors: one solve.  FP32 factors: a solve, then up to refine_sweeps
+// sweeps of r = rhs - W u (FP64, with the FP64 Jacobian), u += W32^-1 r, until the last
+// correction is below 1e-5 of the error-control scale atol + rtol |y|.  Returns false if it
+// did not get there.
+template <int G>
+__device__ bool stage_solve(const Grp<G>& g, const CellMem& w, const IntegrateArgs& a, int N, double gh, bool f32,
+                            double* u) {
+  constexpr int NT = Grp<G>::NT;
+  if (!f32) {
+    for (int i = g.t; i < N; i += NT) u[i] = w.rhs[i];
+    g.sync();
+    cell_solve(g, w.B, N, w.perm, w.invdiag, u);
+    return true;
+  }
+  const float* S = reinterpret_cast<const float*>(w.B);
+  if (g.warp() == 0) warp_lu_solve32(S, N, w.perm, w.invd32, w.er, w.ec, w.rhs, u);
+  g.sync();
+  double conv = INFINITY;
+  for (int s = 0; s < a.refine_sweeps; ++s) {
+    // residual r = rhs - W u = rhs - gh u + J u
+    for (int i = g.t; i < N; i += NT) {
+      const double* Ji = w.A + (size_t)i * N;
+      double s0 = 0.0, s1 = 0.0;
+      int j = 0;
+      for (; j + 1 < N; j += 2) {
+        s0 = fma(Ji[j], u[j], s0);
+        s1 = fma(Ji[j + 1], u[j + 1], s1);
+      }
+      if (j < N) s0 = fma(Ji[j], u[j], s0);
+      w.res[i] = fma(-gh, u[i], w.rhs[i]) + (s0 + s1);
+    }
+    g.sync();
+    if (g.warp() == 0) warp_lu_solve32(S, N, w.perm, w.invd32, w.er, w.ec, w.res, w.res);
+    g.sync();
+    double c = 0.0;
+    for (int i = g.t; i < N; i += NT) {
+      const double d = w.res[i];
+      u[i] += d;
+      c = Grp<G>::nanmax(c, fabs(d) / (a.atol + a.rtol * fabs(w.y[i])));
+    }
+    conv = g.max_nan(c);
+    if (conv <= 1e-5) break;
+  }
+  return conv <= 1e-5;
+}
+
+template <int G>
+__device__ inline int64_t next_cell(const IntegrateArgs& a, const Grp<G>& g, const CellMem& w, int64_t& static_next,
+                                    int64_t stride) {
   if (a.use_queue) {
-    int c = 0;
-    if ((threadIdx.x & 31) == 0) c = atomicAdd(a.queue, 1);
-    return (int64_t)__shfl_sync(kFull, c, 0);
+    if (g.t == 0) *w.slot = atomicAdd(a.queue, 1);
+    g.sync();
+    const int c = *w.slot;
+    g.sync();
+    return (int64_t)c;
   }
   const int64_t c = static_next;
   static_next += stride;
   return c;
 }
 
+template <int G>
 __global__ void __launch_bounds__(256) integrate_kernel(DevMech m, Plan plan, IntegrateArgs a) {
   extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  WarpMem w = carve(smem + (size_t)wib * plan.total, plan);
+  Grp<G> g;
+  g.t = threadIdx.x % Grp<G>::NT;
+  g.gid = threadIdx.x / Grp<G>::NT;
+  g.parity = 0;
+  CellMem w = carve(smem + (size_t)g.gid * plan.total, plan);
+  g.red = w.red;
+  constexpr int NT = Grp<G>::NT;
   const int N = m.N, K = m.K;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  int64_t static_next = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  const int groups_per_cta = blockDim.x / NT;
+  const int64_t ngroups = (int64_t)gridDim.x * groups_per_cta;
+  int64_t static_next = (int64_t)blockIdx.x * groups_per_cta + g.gid;
   const double gam = c_gamma;
   for (;;) {
-    const int64_t cell = next_cell(a, static_next, nwarps);
+    const int64_t cell = next_cell(a, g, w, static_next, ngroups);
     if (cell >= a.ncells) break;
     // load the state phi = [T, Y_1..Y_{K-1}]
-    bool bad = false;
-    for (int i = lane; i < N; i += 32) {
+    int bad = 0;
+    for (int i = g.t; i < N; i += NT) {
       const double v = (i == 0) ? a.T[cell] : a.Y[(size_t)(i - 1) * a.ncells + cell];
       w.y[i] = v;
       bad |= !isfinite(v);
     }
-    bad = __any_sync(kFull, bad) || !(a.T[cell] > 0.0);
-    int status = CHEM_CELL_OK;
+    bad = (g.sum((double)bad) > 0.0) || !(a.T[cell] > 0.0);
+    int status = bad ? CHEM_CELL_BAD_INPUT : CHEM_CELL_OK;
     int nsteps = 0, nrej = 0;
     double h_next = 0.01 * a.dt;
     if (a.h_inout) {
       const double h0 = a.h_inout[cell];
       if (h0 > 0.0) h_next = fmin(h0, a.dt);
     }
-    if (bad) status = CHEM_CELL_BAD_INPUT;
     double t = 0.0, h = h_next;
     bool need_jac = true, last_rej = false;
-    __syncwarp();
+    int f64_until = 0;
+    g.sync();
     for (int attempt = 0; status == CHEM_CELL_OK; ++attempt) {
       if (attempt >= a.max_steps) { status = CHEM_CELL_MAX_STEPS; break; }
       if (h_next < 1e-14 * a.dt) { status = CHEM_CELL_H_UNDERFLOW; break; }
+      PHASE_BEGIN
       if (need_jac) {
-        const CellScalars s0 = warp_rates(m, a.p, w.y, w.f0, w, w.A, true);
-        warp_jacobian(m, s0, w.f0, w, w.A, w.B);
+        const CellScalars s0 = cell_rates(m, g, a.p, w.y, w.f0, w, w.A, true);
+        PHASE_END(0);
+        cell_jacobian(m, g, s0, w.f0, w, w.A, w.B);
+        PHASE_END(1);
         need_jac = false;
       }
-      // iteration matrix W = I/(gamma h) - J and its LU factors (buffer B)
+      // iteration matrix W = I/(gamma h) - J and its factors.  Mixed precision first tries the
+      // FP32 factors of the equilibrated matrix with FP64-residual refinement; if a stage solve
+      // does not converge the attempt is redone with FP64 factors.
       const double gh = 1.0 / (gam * h);
-      for (int e = lane; e < N * N; e += 32) {
-        const int i = e / N, j = e - i * N;
-        w.B[e] = (i == j ? gh : 0.0) - w.A[e];
-      }
-      __syncwarp();
-      const bool ok = warp_lu(w.B, N, w.piv, w.invdiag);
+      const double invh = 1.0 / h;
       double err = INFINITY;
-      if (ok) {
-        const double invh = 1.0 / h;
+      // after a fallback the next attempts go straight to FP64 factors for a while
+      for (int pass = (a.mixed && attempt >= f64_until) ? 0 : 1; pass < 2; ++pass) {
+        const bool f32 = pass == 0;
+        bool ok;
+        if (f32) {
+          ok = form_and_factor32(g, w, N, gh);
+        } else {
+          for (int e = g.t; e < N * N; e += NT) w.B[e] = -w.A[e];
+          g.sync();
+          for (int i = g.t; i < N; i += NT) w.B[i * N + i] += gh;
+          g.sync();
+          ok = cell_lu<G, double>(g, w.B, N, w.piv, w.perm, w.invdiag);
+        }
+        PHASE_END(2);
+        if (!ok) break;  // exactly singular: reject the attempt
+        bool conv = true;
         // stage 1
-        for (int i = lane; i < N; i += 32) w.u[0][i] = w.f0[i];
-        __syncwarp();
-        warp_lu_solve(w.B, N, w.piv, w.invdiag, w.u[0]);
+        for (int i = g.t; i < N; i += NT) w.rhs[i] = w.f0[i];
+        g.sync();
+        conv = stage_solve(g, w, a, N, gh, f32, w.u[0]);
+        PHASE_END(3);
         // stage 2
-        for (int i = lane; i < N; i += 32) w.ynew[i] = w.y[i] + c_a21 * w.u[0][i];
-        __syncwarp();
-        warp_rates(m, a.p, w.ynew, w.fs, w, nullptr, false);
-        for (int i = lane; i < N; i += 32) w.u[1][i] = w.fs[i] + (c_c21 * invh) * w.u[0][i];
-        __syncwarp();
-        warp_lu_solve(w.B, N, w.piv, w.invdiag, w.u[1]);
+        if (conv) {
+          for (int i = g.t; i < N; i += NT) w.ynew[i] = fma(c_a21, w.u[0][i], w.y[i]);
+          g.sync();
+          cell_rates(m, g, a.p, w.ynew, w.fs, w, nullptr, false);
+          PHASE_END(4);
+          for (int i = g.t; i < N; i += NT) w.rhs[i] = fma(c_c21 * invh, w.u[0][i], w.fs[i]);
+          g.sync();
+          conv = stage_solve(g, w, a, N, gh, f32, w.u[1]);
+          PHASE_END(3);
+        }
         // stage 3
-        for (int i = lane; i < N; i += 32) w.ynew[i] = w.y[i] + c_a31 * w.u[0][i] + c_a32 * w.u[1][i];
-        __syncwarp();
-        warp_rates(m, a.p, w.ynew, w.fs, w, nullptr, false);
-        for (int i = lane; i < N; i += 32)
-          w.u[2][i] = w.fs[i] + invh * (c_c31 * w.u[0][i] + c_c32 * w.u[1][i]);
-        __syncwarp();
-        warp_lu_solve(w.B, N, w.piv, w.invdiag, w.u[2]);
+        if (conv) {
+          for (int i = g.t; i < N; i += NT) w.ynew[i] = w.y[i] + c_a31 * w.u[0][i] + c_a32 * w.u[1][i];
+          g.sync();
+          cell_rates(m, g, a.p, w.ynew, w.fs, w, nullptr, false);
+          PHASE_END(4);
+          for (int i = g.t; i < N; i += NT)
+            w.rhs[i] = w.fs[i] + invh * (c_c31 * w.u[0][i] + c_c32 * w.u[1][i]);
+          g.sync();
+          conv = stage_solve(g, w, a, N, gh, f32, w.u[2]);
+        }
         // stage 4 (same argument as stage 3)
-        for (int i = lane; i < N; i += 32)
-          w.u[3][i] = w.fs[i] + invh * (c_c41 * w.u[0][i] + c_c42 * w.u[1][i] + c_c43 * w.u[2][i]);
-        __syncwarp();
-        warp_lu_solve(w.B, N, w.piv, w.invdiag, w.u[3]);
+        if (conv) {
+          for (int i = g.t; i < N; i += NT)
+            w.rhs[i] = w.fs[i] + invh * (c_c41 * w.u[0][i] + c_c42 * w.u[1][i] + c_c43 * w.u[2][i]);
+          g.sync();
+          conv = stage_solve(g, w, a, N, gh, f32, w.u[3]);
+        }
+        if (!conv) {
+          if (g.t == 0) atomicAdd(&a.totals[3], 1ull);
+          f64_until = attempt + 16;
+          continue;  // redo this attempt with FP64 factors
+        }
         // solution, embedded error, filtered through (I - gamma h J)^-1 = W^-1 / (gamma h)
-        for (int i = lane; i < N; i += 32) {
+        // (the filter only feeds the step-size control, so FP32 factors need no refinement)
+        for (int i = g.t; i < N; i += NT) {
           w.ynew[i] = w.y[i] + c_m[0] * w.u[0][i] + c_m[1] * w.u[1][i] + c_m[2] * w.u[2][i] + c_m[3] * w.u[3][i];
-          w.err[i] = c_e[0] * w.u[0][i] + c_e[1] * w.u[1][i] + c_e[2] * w.u[2][i] + c_e[3] * w.u[3][i];
+          w.rhs[i] = c_e[0] * w.u[0][i] + c_e[1] * w.u[1][i] + c_e[2] * w.u[2][i] + c_e[3] * w.u[3][i];
         }
-        __syncwarp();
-        warp_lu_solve(w.B, N, w.piv, w.invdiag, w.err);
+        g.sync();
+        if (f32) {
+          if (g.warp() == 0)
+            warp_lu_solve32(reinterpret_cast<const float*>(w.B), N, w.perm, w.invd32, w.er, w.ec, w.rhs, w.err);
+          g.sync();
+        } else {
+          for (int i = g.t; i < N; i += NT) w.err[i] = w.rhs[i];
+          g.sync();
+          cell_solve(g, w.B, N, w.perm, w.invdiag, w.err);
+        }
+        PHASE_END(3);
         double e = 0.0;
-        for (int i = lane; i < N; i += 32) {
+        for (int i = g.t; i < N; i += NT) {
           const double sc = a.atol + a.rtol * fmax(fabs(w.y[i]), fabs(w.ynew[i]));
-          e = nanmax(e, fabs(w.err[i] * gh) / sc);
+          e = Grp<G>::nanmax(e, fabs(w.err[i] * gh) / sc);
         }
-        err = warp_max_nan(e);
+        err = g.max_nan(e);
+        break;
       }
       double fac;
       if (err <= 1.0) {
         t = (h >= a.dt - t) ? a.dt : t + h;
-        for (int i = lane; i < N; i += 32) w.y[i] = w.ynew[i];
-        __syncwarp();
+        for (int i = g.t; i < N; i += NT) w.y[i] = w.ynew[i];
+        g.sync();
         ++nsteps;
         need_jac = true;
         fac = fmin(6.0, fmax(0.2, 0.9 * pow(err, -0.25)));
@@ -620,16 +1003,17 @@ __global__ void __launch_bounds__(256) integrate_kernel(DevMech m, Plan plan, In
         h_next = h * fac;
       }
       h = fmin(h_next, a.dt - t);
+      PHASE_END(5);
     }
     // store phi and Y_K = 1 - sum
     double ysum = 0.0;
-    for (int i = lane; i < N; i += 32) {
+    for (int i = g.t; i < N; i += NT) {
       const double v = w.y[i];
       if (i == 0) a.T[cell] = v;
       else { a.Y[(size_t)(i - 1) * a.ncells + cell] = v; ysum += v; }
     }
-    ysum = warp_sum(ysum);
-    if (lane == 0) {
+    ysum = g.sum(ysum);
+    if (g.t == 0) {
       if (status != CHEM_CELL_BAD_INPUT) a.Y[(size_t)(K - 1) * a.ncells + cell] = 1.0 - ysum;
       if (a.h_inout && status != CHEM_CELL_BAD_INPUT) a.h_inout[cell] = h_next;
       if (a.status) a.status[cell] = status;
@@ -639,33 +1023,50 @@ __global__ void __launch_bounds__(256) integrate_kernel(DevMech m, Plan plan, In
       atomicAdd(&a.totals[1], (unsigned long long)nrej);
       if (status != CHEM_CELL_OK) atomicAdd(&a.totals[2], 1ull);
     }
-    __syncwarp();
+    g.sync();
   }
 }
 
 // One-shot source term / Jacobian for chem_rates and chem_jacobian.
+template <int G>
 __global__ void __launch_bounds__(256) rates_kernel(DevMech m, Plan plan, double p, const double* T, const double* Y,
-                                                     int64_t ncells, double* out_f, double* out_J) {
+                                                    int64_t ncells, double* out_f, double* out_J) {
   extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  WarpMem w = carve(smem + (size_t)wib * plan.total, plan);
+  Grp<G> g;
+  g.t = threadIdx.x % Grp<G>::NT;
+  g.gid = threadIdx.x / Grp<G>::NT;
+  g.parity = 0;
+  CellMem w = carve(smem + (size_t)g.gid * plan.total, plan);
+  g.red = w.red;
+  constexpr int NT = Grp<G>::NT;
   const int N = m.N;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t cell = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; cell < ncells; cell += nwarps) {
-    for (int i = lane; i < N; i += 32) w.y[i] = (i == 0) ? T[cell] : Y[(size_t)(i - 1) * ncells + cell];
-    __syncwarp();
+  const int groups_per_cta = blockDim.x / NT;
+  const int64_t ngroups = (int64_t)gridDim.x * groups_per_cta;
+  for (int64_t cell = (int64_t)blockIdx.x * groups_per_cta + g.gid; cell < ncells; cell += ngroups) {
+    for (int i = g.t; i < N; i += NT) w.y[i] = (i == 0) ? T[cell] : Y[(size_t)(i - 1) * ncells + cell];
+    g.sync();
     const bool jac = out_J != nullptr;
-    CellScalars s = warp_rates(m, p, w.y, w.f0, w, w.A, jac);
+    CellScalars s = cell_rates(m, g, p, w.y, w.f0, w, w.A, jac);
     if (jac) {
-      warp_jacobian(m, s, w.f0, w, w.A, w.B);
+      cell_jacobian(m, g, s, w.f0, w, w.A, w.B);
       double* o = out_J + (size_t)cell * N * N;
-      for (int e = lane; e < N * N; e += 32) o[e] = w.A[e];
+      for (int e = g.t; e < N * N; e += NT) o[e] = w.A[e];
     }
     if (out_f)
-      for (int i = lane; i < N; i += 32) out_f[(size_t)i * ncells + cell] = w.f0[i];
-    __syncwarp();
+      for (int i = g.t; i < N; i += NT) out_f[(size_t)i * ncells + cell] = w.f0[i];
+    g.sync();
   }
+}
+
+// Diagnostic: FP64 FMA pipe throughput (8 independent chains per thread).
+__global__ void __launch_bounds__(256) fp64_peak_kernel(double* out, int iters, double s) {
+  double a0 = threadIdx.x * 1e-3, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6,
+         a7 = a0 + 7;
+  for (int i = 0; i < iters; ++i) {
+    a0 = fma(a0, s, 0.5); a1 = fma(a1, s, 0.5); a2 = fma(a2, s, 0.5); a3 = fma(a3, s, 0.5);
+    a4 = fma(a4, s, 0.5); a5 = fma(a5, s, 0.5); a6 = fma(a6, s, 0.5); a7 = fma(a7, s, 0.5);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
 }
 
 }  // namespace
@@ -676,7 +1077,6 @@ __global__ void __launch_bounds__(256) rates_kernel(DevMech m, Plan plan, double
 struct chem_mech {
   HostMech host;
   DevMech dev;
-  Plan plan;
   void* dbuf = nullptr;
   int device = 0;
   int num_sms = 0;
@@ -741,26 +1141,44 @@ int ensure_stage(chem_mech* m, size_t bytes) {
 }
 
 struct Launch {
-  int warps_per_cta, grid;
+  int G, cells_per_cta, grid, threads;
   size_t smem;
+  Plan plan;
 };
 
-int pick_launch(const chem_mech* m, int64_t ncells, int want_wpc, int want_ctas_per_sm, const void* kernel,
+const void* integrate_fn(int G) {
+  return G == 1 ? (const void*)integrate_kernel<1> : G == 2 ? (const void*)integrate_kernel<2>
+                                                            : (const void*)integrate_kernel<4>;
+}
+const void* rates_fn(int G) {
+  return G == 1 ? (const void*)rates_kernel<1> : G == 2 ? (const void*)rates_kernel<2> : (const void*)rates_kernel<4>;
+}
+
+// Launch shape: G warps per cell (default 2 for mechanisms with >= 32 species, else 1), as many
+// cells per CTA as the shared memory allows (at most 8 warps per CTA, 15 named barriers), one
+// persistent CTA wave.
+int pick_launch(const chem_mech* m, int64_t ncells, int want_G, int want_cpc, int want_ctas_per_sm, bool integ,
                 Launch& L) {
-  const size_t per_warp = (size_t)m->plan.total * sizeof(double);
-  int max_wpc = (int)std::min<size_t>(8, m->max_smem / per_warp);
-  if (max_wpc < 1)
-    return set_err(CHEM_ESIZE, "mechanism working set (" + std::to_string(per_warp) +
+  int G = want_G > 0 ? want_G : (m->host.K >= 32 ? 2 : 1);
+  if (G != 1 && G != 2 && G != 4) return set_err(CHEM_EINVAL, "warps_per_cell must be 1, 2 or 4");
+  L.G = G;
+  L.plan = make_plan(m->host.K, m->host.R, m->dev.n_pd, G);
+  const size_t per_cell = (size_t)L.plan.total * sizeof(double);
+  int max_cpc = (int)std::min<size_t>(std::min(8 / G, 15), m->max_smem / per_cell);
+  if (max_cpc < 1)
+    return set_err(CHEM_ESIZE, "mechanism working set (" + std::to_string(per_cell) +
                                    " B per cell) exceeds the shared memory of one CTA");
-  int wpc = want_wpc > 0 ? std::min(want_wpc, max_wpc) : std::min(4, max_wpc);
-  L.warps_per_cta = wpc;
-  L.smem = per_warp * wpc;
+  const int cpc = want_cpc > 0 ? std::min(want_cpc, max_cpc) : max_cpc;
+  L.cells_per_cta = cpc;
+  L.threads = 32 * G * cpc;
+  L.smem = per_cell * cpc;
+  const void* kernel = integ ? integrate_fn(G) : rates_fn(G);
   int occ = 0;
   CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 32 * wpc, L.smem));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, L.threads, L.smem));
   if (occ < 1) return set_err(CHEM_ESIZE, "kernel cannot be resident with the requested shared memory");
-  int cps = want_ctas_per_sm > 0 ? std::min(want_ctas_per_sm, occ) : occ;
-  int64_t need = (ncells + wpc - 1) / wpc;
+  const int cps = want_ctas_per_sm > 0 ? std::min(want_ctas_per_sm, occ) : occ;
+  const int64_t need = (ncells + cpc - 1) / cpc;
   L.grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)m->num_sms * cps));
   return 0;
 }
@@ -779,6 +1197,7 @@ void chem_default_opts(chem_opts* o) {
   o->use_queue = 1;
   o->cells_per_cta = 0;
   o->ctas_per_sm = 0;
+  o->warps_per_cell = 0;
 }
 
 int chem_load_mechanism(const char* path, chem_mech** out) {
@@ -811,6 +1230,17 @@ int chem_load_mechanism(const char* path, chem_mech** out) {
   const size_t o_fo = place(std::max<size_t>(1, h.fo.size()) * sizeof(double));
   const size_t o_srp = place(h.sr_ptr.size() * sizeof(int));
   const size_t o_sri = place(std::max<size_t>(1, h.sr_idx.size()) * sizeof(int));
+  const size_t o_srn = place(std::max<size_t>(1, h.sr_nu.size()) * sizeof(double));
+  const size_t o_zgp = place(h.zg_ptr.size() * sizeof(int));
+  const size_t o_zgd = place(std::max<size_t>(1, h.zg_dst.size()) * sizeof(int));
+  const size_t o_zgs = place(std::max<size_t>(1, h.zg_src.size()) * sizeof(int));
+  const size_t o_zgs2 = place(std::max<size_t>(1, h.zg_src2.size()) * sizeof(int));
+  const size_t o_zgc = place(std::max<size_t>(1, h.zg_coef.size()) * sizeof(double));
+  const size_t o_prp = place(h.pr_ptr.size() * sizeof(int));
+  const size_t o_prd = place(std::max<size_t>(1, h.pr_pd.size()) * sizeof(int));
+  const size_t o_prn = place(std::max<size_t>(1, h.pr_nu.size()) * sizeof(double));
+  const size_t o_prr = place(std::max<size_t>(1, h.pr_row.size()) * sizeof(int));
+  const size_t o_prs = place(std::max<size_t>(1, h.pr_rows.size()) * sizeof(int));
   const size_t total = off;
   std::vector<char> img(total, 0);
   auto put = [&](size_t o, const void* src, size_t bytes) { if (bytes) std::memcpy(img.data() + o, src, bytes); };
@@ -822,6 +1252,17 @@ int chem_load_mechanism(const char* path, chem_mech** out) {
   put(o_fo, h.fo.data(), h.fo.size() * sizeof(double));
   put(o_srp, h.sr_ptr.data(), h.sr_ptr.size() * sizeof(int));
   put(o_sri, h.sr_idx.data(), h.sr_idx.size() * sizeof(int));
+  put(o_srn, h.sr_nu.data(), h.sr_nu.size() * sizeof(double));
+  put(o_zgp, h.zg_ptr.data(), h.zg_ptr.size() * sizeof(int));
+  put(o_zgd, h.zg_dst.data(), h.zg_dst.size() * sizeof(int));
+  put(o_zgs, h.zg_src.data(), h.zg_src.size() * sizeof(int));
+  put(o_zgs2, h.zg_src2.data(), h.zg_src2.size() * sizeof(int));
+  put(o_zgc, h.zg_coef.data(), h.zg_coef.size() * sizeof(double));
+  put(o_prp, h.pr_ptr.data(), h.pr_ptr.size() * sizeof(int));
+  put(o_prd, h.pr_pd.data(), h.pr_pd.size() * sizeof(int));
+  put(o_prn, h.pr_nu.data(), h.pr_nu.size() * sizeof(double));
+  put(o_prr, h.pr_row.data(), h.pr_row.size() * sizeof(int));
+  put(o_prs, h.pr_rows.data(), h.pr_rows.size() * sizeof(int));
   e = cudaMalloc(&m->dbuf, total);
   if (e == cudaSuccess) e = cudaMemcpy(m->dbuf, img.data(), total, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&m->d_totals, 4 * sizeof(unsigned long long));
@@ -842,10 +1283,27 @@ int chem_load_mechanism(const char* path, chem_mech** out) {
   d.fo = reinterpret_cast<const double*>(b + o_fo);
   d.sr_ptr = reinterpret_cast<const int*>(b + o_srp);
   d.sr_idx = reinterpret_cast<const int*>(b + o_sri);
-  m->plan = make_plan(h.K, h.R, d.n_pd);
-  if ((size_t)m->plan.total * sizeof(double) > m->max_smem) {
+  d.sr_nu = reinterpret_cast<const double*>(b + o_srn);
+  d.zg_entries = (int)h.zg_dst.size();
+  d.zg_ptr = reinterpret_cast<const int*>(b + o_zgp);
+  d.zg_dst = reinterpret_cast<const int*>(b + o_zgd);
+  d.zg_src = reinterpret_cast<const int*>(b + o_zgs);
+  d.zg_src2 = reinterpret_cast<const int*>(b + o_zgs2);
+  d.zg_coef = reinterpret_cast<const double*>(b + o_zgc);
+  d.pr_ptr = reinterpret_cast<const int*>(b + o_prp);
+  d.pr_pd = reinterpret_cast<const int*>(b + o_prd);
+  d.pr_nu = reinterpret_cast<const double*>(b + o_prn);
+  d.pr_row = reinterpret_cast<const int*>(b + o_prr);
+  d.pr_rows = reinterpret_cast<const int*>(b + o_prs);
+  d.n_pairs = (int)h.pr_pd.size();
+  d.n_prows = (int)h.pr_rows.size();
+  if (d.n_pairs > 8 * (((h.K + 1) / 2) * 2)) {
     chem_free_mechanism(m);
-    return set_err(CHEM_ESIZE, "chem_load_mechanism: mechanism too large for one warp's shared memory");
+    return set_err(CHEM_ESIZE, "chem_load_mechanism: too many pressure-dependent (row, reaction) pairs");
+  }
+  if ((size_t)make_plan(h.K, h.R, d.n_pd, 4).total * sizeof(double) > m->max_smem) {
+    chem_free_mechanism(m);
+    return set_err(CHEM_ESIZE, "chem_load_mechanism: mechanism too large for one CTA's shared memory");
   }
   *out = m;
   return CHEM_OK;
@@ -899,9 +1357,14 @@ static int rates_or_jacobian(const chem_mech* mc, double p_Pa, const double* T, 
     dJ = J ? sJ : nullptr;
   }
   Launch L;
-  int rc = pick_launch(m, ncells, 0, 0, (const void*)rates_kernel, L);
+  int rc = pick_launch(m, ncells, 0, 0, 0, false, L);
   if (rc) return rc;
-  rates_kernel<<<L.grid, 32 * L.warps_per_cta, L.smem, st>>>(m->dev, m->plan, p_Pa * 10.0, dT, dY, ncells, df, dJ);
+  if (L.G == 1)
+    rates_kernel<1><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, p_Pa * 10.0, dT, dY, ncells, df, dJ);
+  else if (L.G == 2)
+    rates_kernel<2><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, p_Pa * 10.0, dT, dY, ncells, df, dJ);
+  else
+    rates_kernel<4><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, p_Pa * 10.0, dT, dY, ncells, df, dJ);
   CK(cudaGetLastError());
   if (!dev) {
     if (f) CK(cudaMemcpyAsync(f, df, sizeof(double) * N * ncells, cudaMemcpyDeviceToHost, st));
@@ -936,7 +1399,11 @@ int chem_integrate(const chem_mech* mc, double p_Pa, double* T, double* Y, int64
   chem_default_opts(&o);
   if (opts) o = *opts;
   if (o.max_steps < 1) return set_err(CHEM_EINVAL, "chem_integrate: max_steps < 1");
-  if (o.precision != CHEM_PREC_FP64) return set_err(CHEM_EINVAL, "chem_integrate: unsupported precision mode");
+  if (o.precision != CHEM_PREC_FP64 && o.precision != CHEM_PREC_MIXED)
+    return set_err(CHEM_EINVAL, "chem_integrate: unknown precision mode");
+  if (o.precision == CHEM_PREC_MIXED && (o.refine_sweeps < 1 || o.refine_sweeps > 4))
+    return set_err(CHEM_EINVAL, "chem_integrate: refine_sweeps must be 1..4");
+  if (m->host.K > 128) return set_err(CHEM_ESIZE, "chem_integrate: more than 128 species");
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (ncells == 0) return CHEM_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -962,7 +1429,7 @@ int chem_integrate(const chem_mech* mc, double p_Pa, double* T, double* Y, int64
   CK(cudaMemsetAsync(m->d_totals, 0, 4 * sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(m->d_queue, 0, sizeof(int), st));
   Launch L;
-  rc = pick_launch(m, ncells, o.cells_per_cta, o.ctas_per_sm, (const void*)integrate_kernel, L);
+  rc = pick_launch(m, ncells, o.warps_per_cell, o.cells_per_cta, o.ctas_per_sm, true, L);
   if (rc) return rc;
   IntegrateArgs a;
   a.p = p_Pa * 10.0; a.dt = dt; a.rtol = rtol; a.atol = atol;
@@ -970,7 +1437,13 @@ int chem_integrate(const chem_mech* mc, double p_Pa, double* T, double* Y, int64
   a.steps_out = m->d_steps; a.rej_out = m->d_rej;
   a.totals = m->d_totals; a.queue = m->d_queue;
   a.ncells = ncells; a.max_steps = o.max_steps; a.use_queue = o.use_queue;
-  integrate_kernel<<<L.grid, 32 * L.warps_per_cta, L.smem, st>>>(m->dev, m->plan, a);
+  a.mixed = o.precision == CHEM_PREC_MIXED; a.refine_sweeps = o.refine_sweeps;
+  if (L.G == 1)
+    integrate_kernel<1><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, a);
+  else if (L.G == 2)
+    integrate_kernel<2><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, a);
+  else
+    integrate_kernel<4><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, a);
   CK(cudaGetLastError());
   if (!dev) {
     CK(cudaMemcpyAsync(T, dT, sizeof(double) * ncells, cudaMemcpyDeviceToHost, st));
@@ -989,6 +1462,43 @@ int chem_integrate(const chem_mech* mc, double p_Pa, double* T, double* Y, int64
   } else if (!dev) {
     CK(cudaStreamSynchronize(st));
   }
+  return CHEM_OK;
+}
+
+#ifdef CHEM_PHASE_TIMERS
+// Debug builds only: per-phase cycle totals {rates+J data, J assembly, W+LU, solves, stage
+// rates, control} summed over cell groups since the last call; resets them.
+int chem_debug_phase_cycles(unsigned long long* out8) {
+  CK(cudaMemcpyFromSymbol(out8, g_phase_cycles, sizeof(unsigned long long) * 8));
+  unsigned long long z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  CK(cudaMemcpyToSymbol(g_phase_cycles, z, sizeof(z)));
+  return CHEM_OK;
+}
+#endif
+
+int chem_probe_fp64_peak(double* tflops) {
+  if (!tflops) return set_err(CHEM_EINVAL, "chem_probe_fp64_peak: NULL output");
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 4, threads = 256, iters = 8192;
+  double* buf = nullptr;
+  CK(cudaMalloc(&buf, sizeof(double) * blocks * threads));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  fp64_peak_kernel<<<blocks, threads>>>(buf, iters / 8, 0.999);  // warm-up
+  cudaEventRecord(e0);
+  fp64_peak_kernel<<<blocks, threads>>>(buf, iters, 0.999);
+  cudaEventRecord(e1);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (e != cudaSuccess) return set_err(CHEM_ECUDA, std::string("chem_probe_fp64_peak: ") + cudaGetErrorString(e));
+  *tflops = 2.0 * 8.0 * (double)iters * blocks * threads / (ms * 1e-3) / 1e12;
   return CHEM_OK;
 }
 

@@ -62,6 +62,79 @@ struct FileReaction {
   std::vector<double> eff;
 };
 
+// Gather plan of the Jacobian's mass-action part and the row lists of its efficiency part.
+// Per-reaction scratch layout (see the kernels): [0..3] dq/dC at the distinct slot species,
+// [4] phi, [5] sum_j dq/dC_j C_j, [6] dq/dT, [7] reaction enthalpy.
+void build_jacobian_plan(HostMech& m) {
+  const int K = m.K, d = K - 1;
+  struct Contrib { int dst, src, src2; double coef; };
+  std::vector<Contrib> cs;
+  for (int r = 0; r < m.R; ++r) {
+    const int* ii = &m.rxi[(size_t)r * kRxInts];
+    for (int u = 0; u < 4; ++u) {
+      const int col = ii[4 + u];
+      if (col < 0) continue;
+      for (int rs = 0; rs < 4; ++rs) {
+        const int row = ii[8 + rs];
+        if (row < 0) continue;
+        cs.push_back({row * K + col, r * 8 + u, -1, (double)ii[12 + rs]});
+      }
+      cs.push_back({d * K + col, r * 8 + u, r * 8 + 7, 1.0});
+    }
+  }
+  std::stable_sort(cs.begin(), cs.end(), [](const Contrib& a, const Contrib& b) { return a.dst < b.dst; });
+  // entries, then ordered by decreasing list length so that threads of a pass get similar work
+  std::vector<std::pair<int, int>> ent;  // (begin, end) into cs
+  for (size_t i = 0; i < cs.size();) {
+    size_t j = i;
+    while (j < cs.size() && cs[j].dst == cs[i].dst) ++j;
+    ent.push_back({(int)i, (int)j});
+    i = j;
+  }
+  std::stable_sort(ent.begin(), ent.end(),
+                   [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+                     return (a.second - a.first) > (b.second - b.first);
+                   });
+  m.zg_ptr.assign(1, 0);
+  m.zg_dst.clear(); m.zg_src.clear(); m.zg_src2.clear(); m.zg_coef.clear();
+  for (const auto& e : ent) {
+    m.zg_dst.push_back(cs[e.first].dst);
+    for (int i = e.first; i < e.second; ++i) {
+      m.zg_src.push_back(cs[i].src);
+      m.zg_src2.push_back(cs[i].src2);
+      m.zg_coef.push_back(cs[i].coef);
+    }
+    m.zg_ptr.push_back((int)m.zg_src.size());
+  }
+  // efficiency rows
+  m.pr_ptr.assign(K + 1, 0);
+  m.pr_pd.clear(); m.pr_nu.clear();
+  const int npd = m.n_tb + m.n_fo;
+  for (int k = 0; k < K; ++k) {
+    m.pr_ptr[k] = (int)m.pr_pd.size();
+    for (int p = 0; p < npd; ++p) {
+      const int* ii = &m.rxi[(size_t)p * kRxInts];
+      if (k < d) {
+        for (int rs = 0; rs < 4; ++rs)
+          if (ii[8 + rs] == k) { m.pr_pd.push_back(p); m.pr_nu.push_back((double)ii[12 + rs]); }
+      } else {
+        m.pr_pd.push_back(p);
+        m.pr_nu.push_back(0.0);
+      }
+    }
+  }
+  m.pr_ptr[K] = (int)m.pr_pd.size();
+  m.pr_row.assign(m.pr_pd.size(), 0);
+  m.pr_rows.clear();
+  for (int k = 0; k < K; ++k) {
+    for (int c = m.pr_ptr[k]; c < m.pr_ptr[k + 1]; ++c) m.pr_row[c] = k;
+    if (m.pr_ptr[k + 1] > m.pr_ptr[k]) m.pr_rows.push_back(k);
+  }
+  std::stable_sort(m.pr_rows.begin(), m.pr_rows.end(), [&](int a, int b) {
+    return (m.pr_ptr[a + 1] - m.pr_ptr[a]) < (m.pr_ptr[b + 1] - m.pr_ptr[b]);
+  });
+}
+
 }  // namespace
 
 bool parse_mechanism(const char* path, HostMech& m, std::string& err) {
@@ -134,10 +207,11 @@ bool parse_mechanism(const char* path, HostMech& m, std::string& err) {
         return fail("missing troe line");
     }
   }
-  // device order: elementary, third-body, Lindemann, Troe (stable within each kind)
+  // device order: Troe, Lindemann, third-body, elementary (stable within each kind): the
+  // fall-off reactions, the costliest, fill whole 32-lane passes from index 0
   m.R = R;
   m.order.clear();
-  for (int t = 0; t <= 3; ++t)
+  for (int t = 3; t >= 0; --t)
     for (int r = 0; r < R; ++r)
       if (rx[r].type == t) m.order.push_back(r);
   m.n_elem = m.n_tb = m.n_fo = 0;
@@ -177,19 +251,20 @@ bool parse_mechanism(const char* path, HostMech& m, std::string& err) {
         if (ii[2 + s] == sp) nu += 1;
       }
       nu_of[u] = nu;
-      if (nu != 0) sr[sp].push_back(dr * 8 + (nu + 4));
+      if (nu != 0) sr[sp].push_back(dr * 8 + (nu + 4));  // reaction and coefficient, unpacked below
     }
     int nrow = 0;
     for (int u = 0; u < uc; ++u)
       if (nu_of[u] != 0 && ii[4 + u] < K - 1) { ii[8 + nrow] = ii[4 + u]; ii[12 + nrow] = nu_of[u]; ++nrow; }
     for (int s = nrow; s < 4; ++s) ii[12 + s] = 0;
+    for (int s = 0; s < 4; ++s) d[3 + s] = (double)ii[12 + s];
     m.dnu[dr] = (ii[2] >= 0) + (ii[3] >= 0) - (ii[0] >= 0) - (ii[1] >= 0);
     if (x.type >= 1) {
-      int pd = dr - m.n_elem;
+      const int pd = dr;  // pressure-dependent reactions come first
       for (int k = 0; k < K; ++k) m.eff[(size_t)pd * K + k] = x.eff[k];
     }
     if (x.type >= 2) {
-      int f = dr - m.n_elem - m.n_tb;
+      const int f = dr;  // fall-off reactions come first of all
       double* q = &m.fo[(size_t)f * kFoDoubles];
       q[0] = std::log(x.A0); q[1] = x.b0; q[2] = x.Ea0 / kRcal;
       q[3] = x.troe[0]; q[4] = x.troe[1]; q[5] = x.troe[2]; q[6] = x.troe[3];
@@ -198,11 +273,16 @@ bool parse_mechanism(const char* path, HostMech& m, std::string& err) {
   }
   m.sr_ptr.assign(K + 1, 0);
   m.sr_idx.clear();
+  m.sr_nu.clear();
   for (int k = 0; k < K; ++k) {
     m.sr_ptr[k] = (int)m.sr_idx.size();
-    m.sr_idx.insert(m.sr_idx.end(), sr[k].begin(), sr[k].end());
+    for (int code : sr[k]) {
+      m.sr_idx.push_back(code >> 3);
+      m.sr_nu.push_back((double)((code & 7) - 4));
+    }
   }
   m.sr_ptr[K] = (int)m.sr_idx.size();
+  build_jacobian_plan(m);
   return true;
 }
 

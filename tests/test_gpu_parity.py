@@ -194,3 +194,18 @@ def test_step_carry_over(small):
     Tg2, Yg2, _, st2, steps2, _ = _gpu_integrate(mech, w, Tg, Yg, h=hg)
     To2, Yo2, _, steps_o2, _ = ora.integrate(w["p_Pa"], To, Yo, w["dt"], h_inout=ho)
     _assert_state_close(Tg2, Yg2, To2, Yo2)
+
+
+@pytest.mark.parametrize("which", ["small", "shear"])
+def test_integrate_parity_mixed_precision(which, request):
+    """FP32 LU + FP64-residual refinement matches the FP64 oracle to the same tolerance."""
+    w, mech, ora = request.getfixturevalue(which)
+    idx = np.arange(256) if which == "small" else _sample_shear(16, 3)
+    T, Y = w["T"][idx], w["Y"][:, idx]
+    opts = chem.default_opts(precision=chem.CHEM_PREC_MIXED)
+    Tg, Yg, sg, stats, steps, _ = _gpu_integrate(mech, w, T, Y, opts=opts)
+    To, Yo, so, steps_o, _ = ora.integrate(w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], nthreads=16)
+    assert np.all(sg == 0) and np.all(so == 0)
+    _assert_state_close(Tg, Yg, To, Yo)
+    # fallbacks to the FP64 factors are the exception, not the rule
+    assert stats.refine_fallbacks <= 0.01 * (stats.steps + stats.rejects)
