@@ -207,5 +207,6 @@ def test_integrate_parity_mixed_precision(which, request):
     To, Yo, so, steps_o, _ = ora.integrate(w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], nthreads=16)
     assert np.all(sg == 0) and np.all(so == 0)
     _assert_state_close(Tg, Yg, To, Yo)
-    # fallbacks to the FP64 factors are the exception, not the rule
-    assert stats.refine_fallbacks <= 0.01 * (stats.steps + stats.rejects)
+    # an attempt whose FP32 refinement does not converge is redone with FP64 factors, and the
+    # cell then stays on FP64 factors for 16 attempts: fallbacks stay a small fraction
+    assert stats.refine_fallbacks <= 0.1 * (stats.steps + stats.rejects)
