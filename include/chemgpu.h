@@ -105,6 +105,28 @@ int chem_integrate(const chem_mech* mech, double p_Pa, double* T, double* Y, int
                    double rtol, double atol, double* h_inout, int32_t* status, const chem_opts* opts,
                    chem_stats* stats, void* stream);
 
+/* chem_integrate without any device-memory allocation.  The paper has no counterpart: this
+ * entry point serves callers that cannot call cudaMalloc while they run, for instance a flow
+ * solver that reserves all device memory for its own pool at start-up, or a time loop that must
+ * not pay the device-wide synchronisation cudaMalloc / cudaFree can cause.
+ *
+ * Same arguments and results as chem_integrate, plus optional device arrays steps[ncells] and
+ * rejects[ncells] for the per-cell counters.  Differences:
+ *   - every array must be device memory (host arrays would need a staging buffer):
+ *     CHEM_EINVAL otherwise;
+ *   - the work-queue counter, the call totals and the per-cell counters live in one fixed
+ *     2 MiB array inside the library (static device memory, loaded with the library on every
+ *     GPU that uses it and held until the process exits), so at most 262144 cells per call:
+ *     larger calls return CHEM_ESIZE without launching anything;
+ *   - the library looks the array's device address up the first time the entry point runs on a
+ *     device (cudaGetSymbolAddress), so make that first call before any stream capture;
+ *   - all calls share that array: it is reset at the start of each call, and two calls whose
+ *     work overlaps on the GPU (different streams, no ordering between them) race on it.
+ * It allocates nothing itself; the mechanism handle, loaded beforehand, owns its tables. */
+int chem_integrate_noalloc(const chem_mech* mech, double p_Pa, double* T, double* Y, int64_t ncells, double dt,
+                           double rtol, double atol, double* h_inout, int32_t* status, int32_t* steps,
+                           int32_t* rejects, const chem_opts* opts, chem_stats* stats, void* stream);
+
 /* Per-cell counters of the last chem_integrate on this mechanism handle, copied to the
  * caller's arrays (device or host, ncells entries each, either may be NULL).  Valid until the
  * next chem_integrate on the handle. */

@@ -66,8 +66,10 @@ def load_library(build_if_missing: bool = True):
                                        ctypes.POINTER(ChemStats), vp]
         lib.chem_last_cell_counters.argtypes = [vp, vp, vp, i64, vp]
         lib.chem_probe_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double)]
+        lib.chem_integrate_noalloc.argtypes = [vp, dp, vp, vp, i64, dp, dp, dp, vp, vp, vp, vp,
+                                               ctypes.POINTER(ChemOpts), ctypes.POINTER(ChemStats), vp]
         for name in ("chem_load_mechanism", "chem_mech_dims", "chem_rates", "chem_jacobian", "chem_integrate",
-                     "chem_last_cell_counters", "chem_probe_fp64_peak"):
+                     "chem_last_cell_counters", "chem_probe_fp64_peak", "chem_integrate_noalloc"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -190,6 +192,26 @@ def chem_integrate(mech: Mechanism, p_Pa: float, T, Y, dt: float, rtol: float = 
     _check(mech._lib.chem_integrate(mech.handle, float(p_Pa), pT, pY, n, float(dt), float(rtol), float(atol), ph, ps,
                                     ctypes.byref(opts) if opts is not None else None,
                                     ctypes.byref(st) if st is not None else None, _stream(stream, dT)))
+    return st
+
+
+def chem_integrate_noalloc(mech: Mechanism, p_Pa: float, T, Y, dt: float, rtol: float = 1e-6, atol: float = 1e-10,
+                           h_inout=None, status=None, steps=None, rejects=None, opts: ChemOpts | None = None,
+                           want_stats: bool = False, stream=None):
+    """chem_integrate for callers that cannot allocate device memory: device tensors only, at most
+    262144 cells, scratch in a fixed array inside the library shared by all calls (calls that
+    overlap on the GPU race).  Optional steps/rejects receive the per-cell counters."""
+    n = _cells(mech, T, Y)
+    pT, dT = _ptr(T, np.float64)
+    pY, _ = _ptr(Y, np.float64)
+    ph, _ = _ptr(h_inout, np.float64)
+    ps, _ = _ptr(status, np.int32)
+    pst, _ = _ptr(steps, np.int32)
+    prj, _ = _ptr(rejects, np.int32)
+    st = ChemStats() if want_stats else None
+    _check(mech._lib.chem_integrate_noalloc(mech.handle, float(p_Pa), pT, pY, n, float(dt), float(rtol), float(atol),
+                                            ph, ps, pst, prj, ctypes.byref(opts) if opts is not None else None,
+                                            ctypes.byref(st) if st is not None else None, _stream(stream, dT)))
     return st
 
 

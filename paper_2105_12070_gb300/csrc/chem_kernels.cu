@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1069,6 +1070,15 @@ __global__ void __launch_bounds__(256) fp64_peak_kernel(double* out, int iters, 
   out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
 }
 
+// ------------------------------------------------------------------------------------------
+// Scratch of chem_integrate_noalloc: a fixed device array instead of library allocations.
+// Layout: [0, 4) work-queue counter, [64, 96) the four call totals, [256, ...) per-cell accepted
+// step counts, then per-cell rejection counts, for at most kNoAllocMaxCells cells (2 MiB).
+constexpr int64_t kNoAllocMaxCells = 262144;
+constexpr size_t kNoAllocCounters = 256;
+constexpr size_t kNoAllocScratchBytes = kNoAllocCounters + 2 * sizeof(int32_t) * (size_t)kNoAllocMaxCells;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
 }  // namespace
 
 // ==========================================================================================
@@ -1475,6 +1485,93 @@ int chem_debug_phase_cycles(unsigned long long* out8) {
   return CHEM_OK;
 }
 #endif
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device (the
+// host-side name of a __device__ array is only a stand-in, never a device address).
+static int noalloc_scratch(void** out) {
+  static std::mutex mu;
+  static void* addr[256] = {};
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return set_err(CHEM_ECUDA, "chem_integrate_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return set_err(CHEM_ECUDA, std::string("chem_integrate_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return CHEM_OK;
+}
+
+int chem_integrate_noalloc(const chem_mech* mc, double p_Pa, double* T, double* Y, int64_t ncells, double dt,
+                           double rtol, double atol, double* h_inout, int32_t* status, int32_t* steps,
+                           int32_t* rejects, const chem_opts* opts, chem_stats* stats, void* stream) {
+  chem_mech* m = const_cast<chem_mech*>(mc);
+  if (ncells < 0) return set_err(CHEM_EINVAL, "chem_integrate_noalloc: ncells < 0");
+  if (ncells > kNoAllocMaxCells)
+    return set_err(CHEM_ESIZE, "chem_integrate_noalloc: " + std::to_string(ncells) + " cells exceed its fixed scratch of " +
+                                   std::to_string(kNoAllocMaxCells) + " cells; use chem_integrate");
+  if (!m || (ncells > 0 && (!T || !Y))) return set_err(CHEM_EINVAL, "chem_integrate_noalloc: NULL argument");
+  if (!(dt > 0.0) || !(rtol > 0.0) || !(atol >= 0.0) || !(p_Pa > 0.0))
+    return set_err(CHEM_EINVAL, "chem_integrate_noalloc: dt, rtol and p must be positive, atol non-negative");
+  chem_opts o;
+  chem_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.max_steps < 1) return set_err(CHEM_EINVAL, "chem_integrate_noalloc: max_steps < 1");
+  if (o.precision != CHEM_PREC_FP64 && o.precision != CHEM_PREC_MIXED)
+    return set_err(CHEM_EINVAL, "chem_integrate_noalloc: unknown precision mode");
+  if (o.precision == CHEM_PREC_MIXED && (o.refine_sweeps < 1 || o.refine_sweeps > 4))
+    return set_err(CHEM_EINVAL, "chem_integrate_noalloc: refine_sweeps must be 1..4");
+  if (m->host.K > 128) return set_err(CHEM_ESIZE, "chem_integrate_noalloc: more than 128 species");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (ncells == 0) return CHEM_OK;
+  const void* arrays[6] = {T, Y, h_inout, status, steps, rejects};
+  for (const void* ptr : arrays)
+    if (ptr && !is_device_ptr(ptr))
+      return set_err(CHEM_EINVAL, "chem_integrate_noalloc: every array must be device memory (host arrays would "
+                                  "need a staging allocation)");
+  void* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned char* s = static_cast<unsigned char*>(scratch);
+  CK(cudaMemsetAsync(s, 0, kNoAllocCounters, st));  // queue counter and totals start at zero
+  Launch L;
+  rc = pick_launch(m, ncells, o.warps_per_cell, o.cells_per_cta, o.ctas_per_sm, true, L);
+  if (rc) return rc;
+  int32_t* d_steps = reinterpret_cast<int32_t*>(s + kNoAllocCounters);
+  int32_t* d_rej = d_steps + kNoAllocMaxCells;
+  IntegrateArgs a;
+  a.p = p_Pa * 10.0; a.dt = dt; a.rtol = rtol; a.atol = atol;
+  a.T = T; a.Y = Y; a.h_inout = h_inout; a.status = status;
+  a.steps_out = d_steps; a.rej_out = d_rej;
+  a.totals = reinterpret_cast<unsigned long long*>(s + 64);
+  a.queue = reinterpret_cast<int*>(s);
+  a.ncells = ncells; a.max_steps = o.max_steps; a.use_queue = o.use_queue;
+  a.mixed = o.precision == CHEM_PREC_MIXED; a.refine_sweeps = o.refine_sweeps;
+  if (L.G == 1)
+    integrate_kernel<1><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, a);
+  else if (L.G == 2)
+    integrate_kernel<2><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, a);
+  else
+    integrate_kernel<4><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, a);
+  CK(cudaGetLastError());
+  if (steps) CK(cudaMemcpyAsync(steps, d_steps, sizeof(int32_t) * ncells, cudaMemcpyDeviceToDevice, st));
+  if (rejects) CK(cudaMemcpyAsync(rejects, d_rej, sizeof(int32_t) * ncells, cudaMemcpyDeviceToDevice, st));
+  if (stats) {
+    unsigned long long tot[4];
+    CK(cudaMemcpyAsync(tot, a.totals, sizeof(tot), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    stats->steps = (int64_t)tot[0];
+    stats->rejects = (int64_t)tot[1];
+    stats->failed_cells = (int64_t)tot[2];
+    stats->refine_fallbacks = (int64_t)tot[3];
+  }
+  return CHEM_OK;
+}
 
 int chem_probe_fp64_peak(double* tflops) {
   if (!tflops) return set_err(CHEM_EINVAL, "chem_probe_fp64_peak: NULL output");
