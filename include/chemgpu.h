@@ -139,6 +139,10 @@ int chem_last_cell_counters(const chem_mech* mech, int32_t* steps, int32_t* reje
  * benchmark reports for the integrate kernel, measured in the same process and clock state. */
 int chem_probe_fp64_peak(double* tflops);
 
+/* Diagnostic for the tests: y[i] = the exponential the rate kernels use (table-driven, Tang
+ * 1989) of x[i], n entries, device arrays, asynchronous on `stream`. */
+int chem_debug_exp(const double* x, double* y, int64_t n, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* chem_last_error(void);
 

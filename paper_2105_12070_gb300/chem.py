@@ -66,10 +66,12 @@ def load_library(build_if_missing: bool = True):
                                        ctypes.POINTER(ChemStats), vp]
         lib.chem_last_cell_counters.argtypes = [vp, vp, vp, i64, vp]
         lib.chem_probe_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double)]
+        lib.chem_debug_exp.argtypes = [vp, vp, i64, vp]
         lib.chem_integrate_noalloc.argtypes = [vp, dp, vp, vp, i64, dp, dp, dp, vp, vp, vp, vp,
                                                ctypes.POINTER(ChemOpts), ctypes.POINTER(ChemStats), vp]
         for name in ("chem_load_mechanism", "chem_mech_dims", "chem_rates", "chem_jacobian", "chem_integrate",
-                     "chem_last_cell_counters", "chem_probe_fp64_peak", "chem_integrate_noalloc"):
+                     "chem_last_cell_counters", "chem_probe_fp64_peak", "chem_integrate_noalloc",
+                     "chem_debug_exp"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -229,3 +231,14 @@ def chem_probe_fp64_peak() -> float:
     if lib.chem_probe_fp64_peak(ctypes.byref(v)) != 0:
         raise ChemError(lib.chem_last_error().decode())
     return v.value
+
+
+def chem_debug_exp(x, out, stream=None):
+    """out = the rate kernels' exponential of x (device float64 tensors), for the tests."""
+    lib = load_library()
+    px, dev = _ptr(x, np.float64)
+    po, _ = _ptr(out, np.float64)
+    rc = lib.chem_debug_exp(px, po, int(x.numel()), _stream(stream, dev))
+    if rc != 0:
+        raise ChemError(lib.chem_last_error().decode())
+    return out

@@ -42,16 +42,16 @@ struct HostMech {
   std::vector<int> sr_ptr;             // [K + 1]
   std::vector<int> sr_idx;             // reaction index (device order)
   std::vector<double> sr_nu;           // net coefficient of the species in that reaction
-  // Jacobian gather plan (mass-action part).  Z entries (row k < K-1 or the enthalpy row K-1,
-  // column j) that receive contributions, each a list of (per-reaction scratch index src,
-  // optional second factor src2 or -1, coefficient): Z[dst] = sum coef * s[src] * s[src2].
+  // Jacobian gather plan (mass-action part).  Z entries (species row k < K-1, column j) that
+  // receive contributions, each a list of (per-reaction scratch index src, coefficient):
+  // Z[dst] = sum coef * s[src].  (src2 is kept for the layout and is always -1.)
   std::vector<int> zg_ptr;             // [n_entries + 1]
   std::vector<int> zg_dst;             // [n_entries] row * K + col
   std::vector<int> zg_src;             // [n_contrib]
   std::vector<int> zg_src2;            // [n_contrib]
   std::vector<double> zg_coef;         // [n_contrib]
-  // Efficiency part: for each row (species k < K-1, then the enthalpy row), the
-  // pressure-dependent reactions in it: (pd index, net coefficient; 0 marks the enthalpy row)
+  // Efficiency part: for each species row k < K-1, the pressure-dependent reactions in it:
+  // (pd index, net coefficient)
   std::vector<int> pr_ptr;             // [K + 1]
   std::vector<int> pr_pd;
   std::vector<double> pr_nu;

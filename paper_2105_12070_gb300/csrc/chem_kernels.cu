@@ -226,6 +226,65 @@ struct CellScalars {
   double T, invT, lnT, rho, inv_rho, Wbar, cp, dcp_dT, fT;
 };
 
+// exp(x) for the rate constants: Tang's table-driven method (P. T. P. Tang, "Table-driven
+// implementation of the exponential function in IEEE floating-point arithmetic", ACM TOMS 15,
+// 1989): x = (32 m + j) ln2/32 + r with |r| <= ln2/64, exp(x) = 2^m 2^(j/32) (1 + p(r)), p the
+// degree-6 Taylor polynomial (truncation below 2e-18), 2^(j/32) as a double-double.  About 12
+// FP64 operations instead of a library call's ~17; |x| >= 708 and NaN go to exp().
+__device__ const double c_exp2_j32[64] = {
+    0x1.0000000000000p+0, 0x0.0p+0,
+    0x1.059b0d3158574p+0, 0x1.d73e2a475b465p-55,
+    0x1.0b5586cf9890fp+0, 0x1.8a62e4adc610bp-54,
+    0x1.11301d0125b51p+0, -0x1.6c51039449b3ap-54,
+    0x1.172b83c7d517bp+0, -0x1.19041b9d78a76p-55,
+    0x1.1d4873168b9aap+0, 0x1.e016e00a2643cp-54,
+    0x1.2387a6e756238p+0, 0x1.9b07eb6c70573p-54,
+    0x1.29e9df51fdee1p+0, 0x1.612e8afad1255p-55,
+    0x1.306fe0a31b715p+0, 0x1.6f46ad23182e4p-55,
+    0x1.371a7373aa9cbp+0, -0x1.63aeabf42eae2p-54,
+    0x1.3dea64c123422p+0, 0x1.ada0911f09ebcp-55,
+    0x1.44e086061892dp+0, 0x1.89b7a04ef80d0p-59,
+    0x1.4bfdad5362a27p+0, 0x1.d4397afec42e2p-56,
+    0x1.5342b569d4f82p+0, -0x1.07abe1db13cadp-55,
+    0x1.5ab07dd485429p+0, 0x1.6324c054647adp-54,
+    0x1.6247eb03a5585p+0, -0x1.383c17e40b497p-54,
+    0x1.6a09e667f3bcdp+0, -0x1.bdd3413b26456p-54,
+    0x1.71f75e8ec5f74p+0, -0x1.16e4786887a99p-55,
+    0x1.7a11473eb0187p+0, -0x1.41577ee04992fp-55,
+    0x1.82589994cce13p+0, -0x1.d4c1dd41532d8p-54,
+    0x1.8ace5422aa0dbp+0, 0x1.6e9f156864b27p-54,
+    0x1.93737b0cdc5e5p+0, -0x1.75fc781b57ebcp-57,
+    0x1.9c49182a3f090p+0, 0x1.c7c46b071f2bep-56,
+    0x1.a5503b23e255dp+0, -0x1.d2f6edb8d41e1p-54,
+    0x1.ae89f995ad3adp+0, 0x1.7a1cd345dcc81p-54,
+    0x1.b7f76f2fb5e47p+0, -0x1.5584f7e54ac3bp-56,
+    0x1.c199bdd85529cp+0, 0x1.11065895048ddp-55,
+    0x1.cb720dcef9069p+0, 0x1.503cbd1e949dbp-56,
+    0x1.d5818dcfba487p+0, 0x1.2ed02d75b3707p-55,
+    0x1.dfc97337b9b5fp+0, -0x1.1a5cd4f184b5cp-54,
+    0x1.ea4afa2a490dap+0, -0x1.e9c23179c2893p-54,
+    0x1.f50765b6e4540p+0, 0x1.9d3e12dd8a18bp-54};
+
+__device__ inline double exp_fast(double x) {
+  if (!(fabs(x) < 708.0)) return exp(x);
+  const double shifter = 0x1.8p52;  // adding it rounds x 32/ln2 to an integer in the low bits
+  const double t = fma(x, 0x1.71547652b82fep+5, shifter);
+  const int k = (int)__double2loint(t);
+  const double kd = t - shifter;
+  double r = fma(-kd, 0x1.62e42fefa39efp-6, x);  // ln2/32, high part
+  r = fma(-kd, 0x1.abc9e3b39803fp-61, r);        // ln2/32, low part
+  double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
+  q = fma(r, q, 1.0 / 24.0);
+  q = fma(r, q, 1.0 / 6.0);
+  q = fma(r, q, 0.5);
+  const double p = fma(r * r, q, r);
+  const int j = k & 31;
+  const double th = __ldg(&c_exp2_j32[2 * j]), tl = __ldg(&c_exp2_j32[2 * j + 1]);
+  const double res = fma(th, p, tl) + th;
+  // times 2^(k >> 5): add to the exponent field (the result stays normal for |x| < 708)
+  return __longlong_as_double(__double_as_longlong(res) + ((long long)(k >> 5) << 52));
+}
+
 // 2^k as a double (|k| < 1000), exact.
 __device__ inline double pow2(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
 
@@ -245,7 +304,7 @@ __device__ inline void nasa7(const double* a, double T, double invT, double lnT,
 __device__ inline void troe(const double* fo, double T, double invT, double Pr, double& F, double& dlF,
                             double& dlnF_dT, bool jac) {
   const double a = fo[3], T3 = fo[4], T1 = fo[5], T2 = fo[6];
-  const double e3 = exp(-T / T3), e1 = exp(-T / T1), e2 = exp(-T2 * invT);
+  const double e3 = exp_fast(-T / T3), e1 = exp_fast(-T / T1), e2 = exp_fast(-T2 * invT);
   const double Fcent = (1.0 - a) * e3 + a * e1 + e2;
   const double L = log10(Fcent);
   const double c = -0.4 - 0.67 * L, n = 0.75 - 1.27 * L;
@@ -253,7 +312,7 @@ __device__ inline void troe(const double* fo, double T, double invT, double Pr, 
   const double den = n - 0.14 * (x + c);
   const double f1 = (x + c) / den;
   const double g = 1.0 + f1 * f1;
-  F = exp10(L / g);
+  F = exp_fast(2.302585092994045684 * (L / g));
   dlF = -2.0 * L * f1 / (g * g) * (n / (den * den));
   dlnF_dT = 0.0;
   if (jac) {
@@ -331,13 +390,13 @@ __device__ CellScalars cell_rates(const DevMech& m, const Grp<G>& g, double p, c
     const double Ca0 = w.C[a0], Ca1 = (a1 >= 0) ? w.C[a1] : 1.0;
     const double Cp0 = w.C[p0], Cp1 = (p1 >= 0) ? w.C[p1] : 1.0;
     const double pf = Ca0 * Ca1, pr = Cp0 * Cp1;
-    double kf = exp(fma(rd[1], s.lnT, rd[0]) - rd[2] * s.invT);
+    double kf = exp_fast(fma(rd[1], s.lnT, rd[0]) - rd[2] * s.invT);
     double dG = w.gRT[p0] - w.gRT[a0];
     if (p1 >= 0) dG += w.gRT[p1];
     if (a1 >= 0) dG -= w.gRT[a1];
     const int dnu = m.dnu[r];
     // 1/Kc = exp(sum nu g/RT - dnu ln(Patm/(Ru T)))
-    const double invKc = exp(dG - dnu * ln_patm_rut);
+    const double invKc = exp_fast(dG - dnu * ln_patm_rut);
     double mfac = 1.0, Mr = 0.0;
     double Pr = 0.0, F = 1.0, dlF = 0.0, dlnF_dT = 0.0, k0 = 0.0;
     const bool pd = r < m.n_pd;
@@ -346,7 +405,7 @@ __device__ CellScalars cell_rates(const DevMech& m, const Grp<G>& g, double p, c
     if (pd) Mr = w.M[r];
     if (fo) {
       fop = m.fo + (size_t)r * kFoDoubles;
-      k0 = exp(fma(fop[1], s.lnT, fop[0]) - fop[2] * s.invT);
+      k0 = exp_fast(fma(fop[1], s.lnT, fop[0]) - fop[2] * s.invT);
       Pr = k0 * Mr / kf;
       if (fop[7] != 0.0) troe(fop, s.T, s.invT, Pr, F, dlF, dlnF_dT, jac);
       kf = kf * Pr / (1.0 + Pr) * F;
@@ -412,7 +471,7 @@ __device__ CellScalars cell_rates(const DevMech& m, const Grp<G>& g, double p, c
 
 // Assemble the analytical Jacobian (Sec. 2.3) at the state of the preceding cell_rates(jac)
 // call.  J (overwritten) holds the per-reaction data on entry, Z is N*N scratch, J receives
-// d f / d phi.  Chain rule through C_j = rho Y_j / W_j, rho = p Wbar/(Ru T), Y_K = 1 - sum Y_i;
+// -d f / d phi (stored negated, so that W = I/(gamma h) - J is a copy plus the diagonal).  Chain rule through C_j = rho Y_j / W_j, rho = p Wbar/(Ru T), Y_K = 1 - sum Y_i;
 // Z rows k < K-1 hold d omega_k / dC, row K-1 holds d Q / dC (Q = sum_k H_k omega_k).
 template <int G>
 __device__ void cell_jacobian(const DevMech& m, const Grp<G>& g, const CellScalars& s, const double* f,
@@ -427,24 +486,15 @@ __device__ void cell_jacobian(const DevMech& m, const Grp<G>& g, const CellScala
   for (int e = g.t; e < m.zg_entries; e += NT) {
     double acc = 0.0;
     const int cb = m.zg_ptr[e], ce = m.zg_ptr[e + 1];
-    for (int c = cb; c < ce; ++c) {
-      double v = scr[m.zg_src[c]];
-      const int s2 = m.zg_src2[c];
-      if (s2 >= 0) v *= scr[s2];
-      acc = fma(m.zg_coef[c], v, acc);
-    }
+    for (int c = cb; c < ce; ++c) acc = fma(m.zg_coef[c], scr[m.zg_src[c]], acc);
     Z[m.zg_dst[e]] = acc;
   }
   g.sync();
   // efficiency part of the pressure-dependent reactions: Z[k][j] += sum_r v_kr eff_rj over the
-  // (row k, reaction r) pairs, v_kr = nu_kr phi_r (row K-1, the enthalpy row: dH_r phi_r).
-  // The coefficients go to the stage-vector area first (free while the Jacobian is built).
+  // (row k, reaction r) pairs, v_kr = nu_kr phi_r.  The coefficients go to the stage-vector area
+  // first (free while the Jacobian is built).
   double* v = w.u[0];
-  for (int c = g.t; c < m.n_pairs; c += NT) {
-    const int r = m.pr_pd[c];
-    const double phi = scr[(size_t)r * 8 + 4];
-    v[c] = (m.pr_row[c] < d) ? m.pr_nu[c] * phi : scr[(size_t)r * 8 + 7] * phi;
-  }
+  for (int c = g.t; c < m.n_pairs; c += NT) v[c] = m.pr_nu[c] * scr[(size_t)m.pr_pd[c] * 8 + 4];
   g.sync();
   {
     const float invK = 1.0f / (float)K;
@@ -458,7 +508,10 @@ __device__ void cell_jacobian(const DevMech& m, const Grp<G>& g, const CellScala
     }
   }
   g.sync();
-  // per-species gathers of sum_j dq/dC_j C_j and dq/dT
+  // per-species gathers of sum_j dq/dC_j C_j and dq/dT; enthalpy weights of the species rows
+  const double invWd = m.sp[d * kSpDoubles + 1];
+  const double RuT = kRu * s.T;
+  double* wq = w.res;
   for (int k = g.t; k < d; k += NT) {
     double zc = 0.0, dw = 0.0;
     for (int e = m.sr_ptr[k]; e < m.sr_ptr[k + 1]; ++e) {
@@ -469,21 +522,33 @@ __device__ void cell_jacobian(const DevMech& m, const Grp<G>& g, const CellScala
     }
     w.zc[k] = zc;
     w.dwT[k] = dw;
+    // mass conservation (sum_k W_k omega_k = 0) gives omega_K = -sum_{k<K} (W_k/W_K) omega_k, so
+    // Q = sum_k H_k omega_k = sum_{k<K} (H_k - H_K W_k/W_K) omega_k: the enthalpy row is a
+    // weighted sum of the species rows
+    wq[k] = RuT * (w.hRT[k] - w.hRT[d] * m.sp[k * kSpDoubles] * invWd);
   }
-  double zqc = 0.0, dqt = 0.0;
-  for (int r = g.t; r < m.R; r += NT) {
-    const double dh = scr[(size_t)r * 8 + 7];
-    zqc = fma(dh, scr[(size_t)r * 8 + 5], zqc);
-    dqt = fma(dh, scr[(size_t)r * 8 + 6], dqt);
+  g.sync();
+  // enthalpy row Z_Q[j] = sum_k wq_k Z[k][j] (stored in row K-1), with sum_j Z_Q[j] C_j and
+  // dQ/dT|_C = sum_k wq_k dw_k/dT|_C
+  double zqc = 0.0, dqt = 0.0, cpw = 0.0;
+  for (int j = g.t; j < K; j += NT) {
+    double a0 = 0.0, a1 = 0.0;
+    int k = 0;
+    for (; k + 1 < d; k += 2) {
+      a0 = fma(wq[k], Z[k * N + j], a0);
+      a1 = fma(wq[k + 1], Z[(k + 1) * N + j], a1);
+    }
+    if (k < d) a0 = fma(wq[k], Z[k * N + j], a0);
+    const double zq = a0 + a1;
+    Z[d * N + j] = zq;
+    zqc = fma(zq, w.C[j], zqc);
+    cpw = fma(w.cpR[j], w.omega[j], cpw);
   }
-  zqc = g.sum(zqc);
-  dqt = g.sum(dqt);
-  double cpw = 0.0;
-  for (int k = g.t; k < K; k += NT) cpw = fma(w.cpR[k], w.omega[k], cpw);
+  for (int k = g.t; k < d; k += NT) dqt = fma(wq[k], w.dwT[k], dqt);
+  g.sum2(zqc, dqt);
   cpw = g.sum(cpw) * kRu;
   g.sync();
   // per-row and per-column factors
-  const double invWd = m.sp[d * kSpDoubles + 1];
   for (int k = g.t; k < d; k += NT) {
     const double Wk = m.sp[k * kSpDoubles];
     w.rowA[k] = Wk * invWd * Z[k * N + d];
@@ -502,18 +567,18 @@ __device__ void cell_jacobian(const DevMech& m, const Grp<G>& g, const CellScala
     const double invWi = m.sp[i * kSpDoubles + 1];
     const double dQdY = s.rho * (invWi * Z[d * N + i] - invWd * ZQd) + zqc * ci;
     const double dcpdY = (w.cpR[i] * invWi - cpd) * kRu;
-    J[1 + i] = -dQdY * inv_rhocp - fT * (ci + dcpdY * inv_cp);
+    J[1 + i] = fma(dQdY, inv_rhocp, fT * (ci + dcpdY * inv_cp));
     const double Wk = m.sp[i * kSpDoubles];
-    J[(1 + i) * N] = Wk * s.inv_rho * (w.dwT[i] - w.zc[i] * s.invT) + f[1 + i] * s.invT;
+    J[(1 + i) * N] = -(Wk * s.inv_rho * (w.dwT[i] - w.zc[i] * s.invT) + f[1 + i] * s.invT);
   }
-  if (g.t == 0) J[0] = -(cpw + dqt - zqc * s.invT) * inv_rhocp - fT * (-s.invT + s.dcp_dT * inv_cp);
+  if (g.t == 0) J[0] = (cpw + dqt - zqc * s.invT) * inv_rhocp + fT * (-s.invT + s.dcp_dT * inv_cp);
   const int nb = d * d;
   const float inv_d = 1.0f / (float)d;
   for (int e = g.t; e < nb; e += NT) {
     const int k = (int)(((float)e + 0.5f) * inv_d), i = e - k * d;
     const double Wk = m.sp[k * kSpDoubles];
     const double invWi = m.sp[i * kSpDoubles + 1];
-    J[(1 + k) * N + 1 + i] = fma(w.rowB[k], w.ccol[i], fma(Wk * invWi, Z[k * N + i], -w.rowA[k]));
+    J[(1 + k) * N + 1 + i] = fma(-w.rowB[k], w.ccol[i], fma(-Wk * invWi, Z[k * N + i], w.rowA[k]));
   }
   g.sync();
 }
@@ -606,104 +671,80 @@ __device__ bool cell_lu(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* in
 }
 
 // x <- A^-1 x with the factors of cell_lu, by one warp with x in registers: lane l holds rows
-// l, l+32, l+64, l+96 (N <= 128), so a column step is a shuffle and at most 4 FMAs, without
-// shared-memory round trips or barriers.  perm is the composed row permutation of the LU.
-__device__ void warp_lu_solve(const double* A, int N, const int* perm, const double* invdiag, double* x) {
+// l, l+32, .. (S slots, N <= 32 S), so a column step is a shuffle and one FMA per slot that
+// still holds rows below (forward) or above (backward) the column, without shared-memory round
+// trips or barriers.  The slot loops are unrolled over compile-time bounds so that no FMA is
+// issued for a slot with no active row.  perm is the composed row permutation of the LU.
+// T is double (FP64 factors) or float (mixed precision; then b is scaled by 2^-er on entry and
+// the result by 2^-ec on exit, see form_and_factor32).
+template <int S, typename T>
+__device__ void warp_lu_solve_s(const T* A, int N, const int* perm, const T* invdiag, const int* er, const int* ec,
+                                const double* b, double* x) {
   const int lane = threadIdx.x & 31;
-  double xr[4];
+  T xr[S];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
+  for (int s = 0; s < S; ++s) {
     const int i = lane + 32 * s;
-    xr[s] = (i < N) ? x[perm[i]] : 0.0;
+    T v = T(0);
+    if (i < N) {
+      const int pi = perm[i];
+      v = er ? (T)(b[pi] * pow2(-er[pi])) : (T)b[pi];
+    }
+    xr[s] = v;
   }
   __syncwarp();
-  // forward substitution with the unit lower factor
-  for (int j = 0; j < N - 1; ++j) {
-    const int js = j >> 5, jl = j & 31;
-    const double src = js == 0 ? xr[0] : js == 1 ? xr[1] : js == 2 ? xr[2] : xr[3];
-    const double xj = __shfl_sync(kFull, src, jl);
+  // forward substitution with the unit lower factor: column j in slot jb updates slots >= jb
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      if (32 * s + 31 > j && 32 * s < N) {  // slot holds rows below j (warp-uniform test)
+  for (int jb = 0; jb < S; ++jb) {
+    const int jend = min(32 * jb + 32, N - 1);
+    for (int j = 32 * jb; j < jend; ++j) {
+      const T xj = __shfl_sync(kFull, xr[jb], j & 31);
+#pragma unroll
+      for (int s = jb; s < S; ++s) {
         const int i = lane + 32 * s;
         if (i > j && i < N) xr[s] = fma(-A[i * N + j], xj, xr[s]);
       }
     }
   }
-  // back substitution with the upper factor
-  for (int j = N - 1; j >= 0; --j) {
-    const int js = j >> 5, jl = j & 31;
-    const double src = js == 0 ? xr[0] : js == 1 ? xr[1] : js == 2 ? xr[2] : xr[3];
-    const double xj = __shfl_sync(kFull, src, jl) * invdiag[j];
-    if (lane == jl) {
-      if (js == 0) xr[0] = xj; else if (js == 1) xr[1] = xj; else if (js == 2) xr[2] = xj; else xr[3] = xj;
-    }
+  // back substitution with the upper factor: column j in slot jb updates slots <= jb
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      if (32 * s < j) {  // slot holds rows above j (warp-uniform test)
+  for (int jb = S - 1; jb >= 0; --jb) {
+    for (int j = min(32 * jb + 31, N - 1); j >= 32 * jb; --j) {
+      const T xj = __shfl_sync(kFull, xr[jb], j & 31) * invdiag[j];
+      if (lane == (j & 31)) xr[jb] = xj;
+#pragma unroll
+      for (int s = 0; s <= jb; ++s) {
         const int i = lane + 32 * s;
         if (i < j) xr[s] = fma(-A[i * N + j], xj, xr[s]);
       }
     }
   }
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
+  for (int s = 0; s < S; ++s) {
     const int i = lane + 32 * s;
-    if (i < N) x[i] = xr[s];
+    if (i < N) x[i] = ec ? (double)xr[s] * pow2(-ec[i]) : (double)xr[s];
   }
   __syncwarp();
 }
 
+template <typename T>
+__device__ void warp_lu_solve_any(const T* A, int N, const int* perm, const T* invdiag, const int* er, const int* ec,
+                                  const double* b, double* x) {
+  if (N <= 32) warp_lu_solve_s<1, T>(A, N, perm, invdiag, er, ec, b, x);
+  else if (N <= 64) warp_lu_solve_s<2, T>(A, N, perm, invdiag, er, ec, b, x);
+  else if (N <= 96) warp_lu_solve_s<3, T>(A, N, perm, invdiag, er, ec, b, x);
+  else warp_lu_solve_s<4, T>(A, N, perm, invdiag, er, ec, b, x);
+}
+
+__device__ void warp_lu_solve(const double* A, int N, const int* perm, const double* invdiag, double* x) {
+  warp_lu_solve_any<double>(A, N, perm, invdiag, nullptr, nullptr, x, x);
+}
+
 // Mixed precision: x <- W^-1 b through the FP32 factors of the equilibrated matrix
-// S = D_r W D_c (D_r, D_c powers of two): z = D_r b, S v = z in FP32, x = D_c v.  One warp,
-// v in registers as in warp_lu_solve.
+// S = D_r W D_c (D_r, D_c powers of two): z = D_r b, S v = z in FP32, x = D_c v.
 __device__ void warp_lu_solve32(const float* A, int N, const int* perm, const float* invdiag, const int* er,
                                 const int* ec, const double* b, double* x) {
-  const int lane = threadIdx.x & 31;
-  float xr[4];
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const int i = lane + 32 * s;
-    if (i < N) {
-      const int pi = perm[i];
-      xr[s] = (float)(b[pi] * pow2(-er[pi]));
-    } else {
-      xr[s] = 0.0f;
-    }
-  }
-  for (int j = 0; j < N - 1; ++j) {
-    const int js = j >> 5, jl = j & 31;
-    const float src = js == 0 ? xr[0] : js == 1 ? xr[1] : js == 2 ? xr[2] : xr[3];
-    const float xj = __shfl_sync(kFull, src, jl);
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      if (32 * s + 31 > j && 32 * s < N) {
-        const int i = lane + 32 * s;
-        if (i > j && i < N) xr[s] = fmaf(-A[i * N + j], xj, xr[s]);
-      }
-    }
-  }
-  for (int j = N - 1; j >= 0; --j) {
-    const int js = j >> 5, jl = j & 31;
-    const float src = js == 0 ? xr[0] : js == 1 ? xr[1] : js == 2 ? xr[2] : xr[3];
-    const float xj = __shfl_sync(kFull, src, jl) * invdiag[j];
-    if (lane == jl) {
-      if (js == 0) xr[0] = xj; else if (js == 1) xr[1] = xj; else if (js == 2) xr[2] = xj; else xr[3] = xj;
-    }
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      if (32 * s < j) {
-        const int i = lane + 32 * s;
-        if (i < j) xr[s] = fmaf(-A[i * N + j], xj, xr[s]);
-      }
-    }
-  }
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const int i = lane + 32 * s;
-    if (i < N) x[i] = (double)xr[s] * pow2(-ec[i]);
-  }
-  __syncwarp();
+  warp_lu_solve_any<float>(A, N, perm, invdiag, er, ec, b, x);
 }
 
 template <int G>
@@ -764,7 +805,7 @@ __device__ bool form_and_factor32(const Grp<G>& g, const CellMem& w, int N, doub
   for (int i = g.t; i < N; i += NT) {
     int mx = 0;
     for (int j = 0; j < N; ++j) {
-      const double v = (i == j) ? gh - w.A[i * N + j] : w.A[i * N + j];
+      const double v = (i == j) ? gh + w.A[i * N + j] : w.A[i * N + j];
       mx = max(mx, exp_field(v));
     }
     w.er[i] = mx - 1023;
@@ -773,7 +814,7 @@ __device__ bool form_and_factor32(const Grp<G>& g, const CellMem& w, int N, doub
   for (int j = g.t; j < N; j += NT) {
     int mx = -2100;
     for (int i = 0; i < N; ++i) {
-      const double v = (i == j) ? gh - w.A[i * N + j] : w.A[i * N + j];
+      const double v = (i == j) ? gh + w.A[i * N + j] : w.A[i * N + j];
       const int ef = exp_field(v);
       if (ef > 0) mx = max(mx, ef - 1023 - w.er[i]);
     }
@@ -782,7 +823,7 @@ __device__ bool form_and_factor32(const Grp<G>& g, const CellMem& w, int N, doub
   g.sync();
   for (int e = g.t; e < N * N; e += NT) {
     const int i = e / N, j = e - (e / N) * N;
-    const double v = (i == j) ? gh - w.A[e] : -w.A[e];
+    const double v = (i == j) ? gh + w.A[e] : w.A[e];
     S[e] = (float)(v * pow2(-w.er[i] - w.ec[j]));
   }
   g.sync();
@@ -808,7 +849,7 @@ __device__ bool stage_solve(const Grp<G>& g, const CellMem& w, const IntegrateAr
   g.sync();
   double conv = INFINITY;
   for (int s = 0; s < a.refine_sweeps; ++s) {
-    // residual r = rhs - W u = rhs - gh u + J u
+    // residual r = rhs - W u = rhs - gh u + J u (the buffer holds -J)
     for (int i = g.t; i < N; i += NT) {
       const double* Ji = w.A + (size_t)i * N;
       double s0 = 0.0, s1 = 0.0;
@@ -818,7 +859,7 @@ __device__ bool stage_solve(const Grp<G>& g, const CellMem& w, const IntegrateAr
         s1 = fma(Ji[j + 1], u[j + 1], s1);
       }
       if (j < N) s0 = fma(Ji[j], u[j], s0);
-      w.res[i] = fma(-gh, u[i], w.rhs[i]) + (s0 + s1);
+      w.res[i] = fma(-gh, u[i], w.rhs[i]) - (s0 + s1);
     }
     g.sync();
     if (g.warp() == 0) warp_lu_solve32(S, N, w.perm, w.invd32, w.er, w.ec, w.res, w.res);
@@ -911,7 +952,7 @@ __global__ void __launch_bounds__(256) integrate_kernel(DevMech m, Plan plan, In
         if (f32) {
           ok = form_and_factor32(g, w, N, gh);
         } else {
-          for (int e = g.t; e < N * N; e += NT) w.B[e] = -w.A[e];
+          for (int e = g.t; e < N * N; e += NT) w.B[e] = w.A[e];
           g.sync();
           for (int i = g.t; i < N; i += NT) w.B[i * N + i] += gh;
           g.sync();
@@ -1051,7 +1092,7 @@ __global__ void __launch_bounds__(256) rates_kernel(DevMech m, Plan plan, double
     if (jac) {
       cell_jacobian(m, g, s, w.f0, w, w.A, w.B);
       double* o = out_J + (size_t)cell * N * N;
-      for (int e = g.t; e < N * N; e += NT) o[e] = w.A[e];
+      for (int e = g.t; e < N * N; e += NT) o[e] = -w.A[e];
     }
     if (out_f)
       for (int i = g.t; i < N; i += NT) out_f[(size_t)i * ncells + cell] = w.f0[i];
@@ -1078,6 +1119,11 @@ constexpr int64_t kNoAllocMaxCells = 262144;
 constexpr size_t kNoAllocCounters = 256;
 constexpr size_t kNoAllocScratchBytes = kNoAllocCounters + 2 * sizeof(int32_t) * (size_t)kNoAllocMaxCells;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+__global__ void exp_probe_kernel(const double* x, double* y, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = exp_fast(x[i]);
+}
 
 }  // namespace
 
@@ -1570,6 +1616,17 @@ int chem_integrate_noalloc(const chem_mech* mc, double p_Pa, double* T, double* 
     stats->failed_cells = (int64_t)tot[2];
     stats->refine_fallbacks = (int64_t)tot[3];
   }
+  return CHEM_OK;
+}
+
+int chem_debug_exp(const double* x, double* y, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return set_err(CHEM_EINVAL, "chem_debug_exp: bad arguments");
+  if (n == 0) return CHEM_OK;
+  if (!is_device_ptr(x) || !is_device_ptr(y)) return set_err(CHEM_EINVAL, "chem_debug_exp: device arrays only");
+  const int threads = 256;
+  const int64_t blocks = (n + threads - 1) / threads;
+  exp_probe_kernel<<<(unsigned)blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(x, y, n);
+  CK(cudaGetLastError());
   return CHEM_OK;
 }
 

@@ -62,7 +62,8 @@ struct FileReaction {
   std::vector<double> eff;
 };
 
-// Gather plan of the Jacobian's mass-action part and the row lists of its efficiency part.
+// Gather plan of the Jacobian's mass-action part and the row lists of its efficiency part, for
+// the species rows k < K-1 (the enthalpy row follows from them, see the kernels).
 // Per-reaction scratch layout (see the kernels): [0..3] dq/dC at the distinct slot species,
 // [4] phi, [5] sum_j dq/dC_j C_j, [6] dq/dT, [7] reaction enthalpy.
 void build_jacobian_plan(HostMech& m) {
@@ -79,7 +80,6 @@ void build_jacobian_plan(HostMech& m) {
         if (row < 0) continue;
         cs.push_back({row * K + col, r * 8 + u, -1, (double)ii[12 + rs]});
       }
-      cs.push_back({d * K + col, r * 8 + u, r * 8 + 7, 1.0});
     }
   }
   std::stable_sort(cs.begin(), cs.end(), [](const Contrib& a, const Contrib& b) { return a.dst < b.dst; });
@@ -112,15 +112,10 @@ void build_jacobian_plan(HostMech& m) {
   const int npd = m.n_tb + m.n_fo;
   for (int k = 0; k < K; ++k) {
     m.pr_ptr[k] = (int)m.pr_pd.size();
-    for (int p = 0; p < npd; ++p) {
+    for (int p = 0; p < npd && k < d; ++p) {
       const int* ii = &m.rxi[(size_t)p * kRxInts];
-      if (k < d) {
-        for (int rs = 0; rs < 4; ++rs)
-          if (ii[8 + rs] == k) { m.pr_pd.push_back(p); m.pr_nu.push_back((double)ii[12 + rs]); }
-      } else {
-        m.pr_pd.push_back(p);
-        m.pr_nu.push_back(0.0);
-      }
+      for (int rs = 0; rs < 4; ++rs)
+        if (ii[8 + rs] == k) { m.pr_pd.push_back(p); m.pr_nu.push_back((double)ii[12 + rs]); }
     }
   }
   m.pr_ptr[K] = (int)m.pr_pd.size();
