@@ -60,7 +60,13 @@ typedef struct {
                         0: static round-robin assignment of cells to warps */
   int cells_per_cta; /* cells in flight per CTA; 0 = automatic */
   int ctas_per_sm;   /* resident CTAs per SM for the persistent grid; 0 = automatic */
-  int warps_per_cell; /* 1, 2 or 4 warps cooperate on one cell; 0 = automatic */
+  int warps_per_cell; /* 1, 2, 4 or 8 warps cooperate on one cell; 0 = automatic */
+  int use_graph;      /* 1: launch through a CUDA graph that the library captures once for this
+                         exact argument set and replays on identical calls (device arrays only);
+                         0 (default): direct launches */
+  int batch_cells;    /* > 0: split the cells into consecutive batches of this many cells, one
+                         kernel launch per batch (the one-launch-per-batch comparison of the
+                         persistent queue); 0 (default): one launch for all cells */
 } chem_opts;
 
 typedef struct {

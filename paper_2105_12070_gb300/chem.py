@@ -26,7 +26,7 @@ CELL_STATUS = {0: "ok", 1: "max_steps", 2: "h_underflow", 3: "bad_input"}
 class ChemOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("refine_sweeps", ctypes.c_int), ("max_steps", ctypes.c_int),
                 ("use_queue", ctypes.c_int), ("cells_per_cta", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-                ("warps_per_cell", ctypes.c_int)]
+                ("warps_per_cell", ctypes.c_int), ("use_graph", ctypes.c_int), ("batch_cells", ctypes.c_int)]
 
 
 class ChemStats(ctypes.Structure):

@@ -786,7 +786,9 @@ struct IntegrateArgs {
   int32_t* rej_out;
   unsigned long long* totals;  // steps, rejects, failed cells, refine fallbacks
   int* queue;
-  int64_t ncells;
+  int64_t ncells;     // number of cells in the arrays (the stride of Y)
+  int64_t first;      // this launch integrates cells first .. first + count - 1
+  int64_t count;
   int max_steps;
   int use_queue;
   int mixed;          // FP32 factors + FP64-residual refinement
@@ -876,23 +878,25 @@ __device__ bool stage_solve(const Grp<G>& g, const CellMem& w, const IntegrateAr
   return conv <= 1e-5;
 }
 
+// Next cell of this group (an index into the arrays), or -1 when the launch's range is done.
 template <int G>
 __device__ inline int64_t next_cell(const IntegrateArgs& a, const Grp<G>& g, const CellMem& w, int64_t& static_next,
                                     int64_t stride) {
+  int64_t c;
   if (a.use_queue) {
     if (g.t == 0) *w.slot = atomicAdd(a.queue, 1);
     g.sync();
-    const int c = *w.slot;
+    c = (int64_t)*w.slot;
     g.sync();
-    return (int64_t)c;
+  } else {
+    c = static_next;
+    static_next += stride;
   }
-  const int64_t c = static_next;
-  static_next += stride;
-  return c;
+  return c < a.count ? a.first + c : -1;
 }
 
 template <int G>
-__global__ void __launch_bounds__(256) integrate_kernel(DevMech m, Plan plan, IntegrateArgs a) {
+__global__ void __launch_bounds__(256, 1) integrate_kernel(DevMech m, Plan plan, IntegrateArgs a) {
   extern __shared__ double smem[];
   Grp<G> g;
   g.t = threadIdx.x % Grp<G>::NT;
@@ -908,7 +912,7 @@ __global__ void __launch_bounds__(256) integrate_kernel(DevMech m, Plan plan, In
   const double gam = c_gamma;
   for (;;) {
     const int64_t cell = next_cell(a, g, w, static_next, ngroups);
-    if (cell >= a.ncells) break;
+    if (cell < 0) break;
     // load the state phi = [T, Y_1..Y_{K-1}]
     int bad = 0;
     for (int i = g.t; i < N; i += NT) {
@@ -1071,7 +1075,7 @@ __global__ void __launch_bounds__(256) integrate_kernel(DevMech m, Plan plan, In
 
 // One-shot source term / Jacobian for chem_rates and chem_jacobian.
 template <int G>
-__global__ void __launch_bounds__(256) rates_kernel(DevMech m, Plan plan, double p, const double* T, const double* Y,
+__global__ void __launch_bounds__(256, 1) rates_kernel(DevMech m, Plan plan, double p, const double* T, const double* Y,
                                                     int64_t ncells, double* out_f, double* out_J) {
   extern __shared__ double smem[];
   Grp<G> g;
@@ -1130,9 +1134,20 @@ __global__ void exp_probe_kernel(const double* x, double* y, int64_t n) {
 // ==========================================================================================
 // Host side
 
+struct GraphKey {
+  IntegrateArgs a;
+  chem_opts o;
+};
+struct GraphCache {
+  GraphKey key;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+};
+
 struct chem_mech {
   HostMech host;
   DevMech dev;
+  GraphCache graph;
   void* dbuf = nullptr;
   int device = 0;
   int num_sms = 0;
@@ -1203,11 +1218,25 @@ struct Launch {
 };
 
 const void* integrate_fn(int G) {
-  return G == 1 ? (const void*)integrate_kernel<1> : G == 2 ? (const void*)integrate_kernel<2>
-                                                            : (const void*)integrate_kernel<4>;
+  return G == 1 ? (const void*)integrate_kernel<1>
+         : G == 2 ? (const void*)integrate_kernel<2>
+         : G == 4 ? (const void*)integrate_kernel<4>
+                  : (const void*)integrate_kernel<8>;
 }
 const void* rates_fn(int G) {
-  return G == 1 ? (const void*)rates_kernel<1> : G == 2 ? (const void*)rates_kernel<2> : (const void*)rates_kernel<4>;
+  return G == 1 ? (const void*)rates_kernel<1>
+         : G == 2 ? (const void*)rates_kernel<2>
+         : G == 4 ? (const void*)rates_kernel<4>
+                  : (const void*)rates_kernel<8>;
+}
+
+void launch_integrate(const Launch& L, cudaStream_t st, const DevMech& d, const IntegrateArgs& a) {
+  switch (L.G) {
+    case 1: integrate_kernel<1><<<L.grid, L.threads, L.smem, st>>>(d, L.plan, a); break;
+    case 2: integrate_kernel<2><<<L.grid, L.threads, L.smem, st>>>(d, L.plan, a); break;
+    case 4: integrate_kernel<4><<<L.grid, L.threads, L.smem, st>>>(d, L.plan, a); break;
+    default: integrate_kernel<8><<<L.grid, L.threads, L.smem, st>>>(d, L.plan, a); break;
+  }
 }
 
 // Launch shape: G warps per cell (default 2 for mechanisms with >= 32 species, else 1), as many
@@ -1216,11 +1245,11 @@ const void* rates_fn(int G) {
 int pick_launch(const chem_mech* m, int64_t ncells, int want_G, int want_cpc, int want_ctas_per_sm, bool integ,
                 Launch& L) {
   int G = want_G > 0 ? want_G : (m->host.K >= 32 ? 2 : 1);
-  if (G != 1 && G != 2 && G != 4) return set_err(CHEM_EINVAL, "warps_per_cell must be 1, 2 or 4");
+  if (G != 1 && G != 2 && G != 4 && G != 8) return set_err(CHEM_EINVAL, "warps_per_cell must be 1, 2, 4 or 8");
   L.G = G;
   L.plan = make_plan(m->host.K, m->host.R, m->dev.n_pd, G);
   const size_t per_cell = (size_t)L.plan.total * sizeof(double);
-  int max_cpc = (int)std::min<size_t>(std::min(8 / G, 15), m->max_smem / per_cell);
+  int max_cpc = (int)std::min<size_t>(std::max(1, std::min(8 / G, 15)), m->max_smem / per_cell);
   if (max_cpc < 1)
     return set_err(CHEM_ESIZE, "mechanism working set (" + std::to_string(per_cell) +
                                    " B per cell) exceeds the shared memory of one CTA");
@@ -1239,6 +1268,51 @@ int pick_launch(const chem_mech* m, int64_t ncells, int want_G, int want_cpc, in
   return 0;
 }
 
+// Enqueue one integrate call on `st`: reset the totals, then for each batch (all cells in one
+// batch unless batch_cells > 0) reset the queue and launch.
+int enqueue_integrate(chem_mech* m, const chem_opts& o, IntegrateArgs a, cudaStream_t st) {
+  CK(cudaMemsetAsync(a.totals, 0, 4 * sizeof(unsigned long long), st));
+  const int64_t total = a.count;
+  const int64_t batch = o.batch_cells > 0 ? (int64_t)o.batch_cells : total;
+  for (int64_t first = 0; first < total; first += batch) {
+    a.first = first;
+    a.count = std::min(batch, total - first);
+    Launch L;
+    int rc = pick_launch(m, a.count, o.warps_per_cell, o.cells_per_cta, o.ctas_per_sm, true, L);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(a.queue, 0, sizeof(int), st));
+    launch_integrate(L, st, m->dev, a);
+    CK(cudaGetLastError());
+  }
+  return 0;
+}
+
+// CUDA-graph launch: the library records enqueue_integrate on its own stream once per argument
+// set (stream capture), instantiates it, and replays it on the caller's stream.
+int launch_via_graph(chem_mech* m, const chem_opts& o, const IntegrateArgs& a, cudaStream_t st) {
+  GraphKey key;
+  std::memset(&key, 0, sizeof(key));
+  key.a = a;
+  key.o = o;
+  GraphCache& gc = m->graph;
+  if (!gc.exec || std::memcmp(&gc.key, &key, sizeof(key)) != 0) {
+    if (gc.exec) { cudaGraphExecDestroy(gc.exec); gc.exec = nullptr; }
+    if (!gc.capture_stream) CK(cudaStreamCreateWithFlags(&gc.capture_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(gc.capture_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_integrate(m, o, a, gc.capture_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(gc.capture_stream, &graph);
+    if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e != cudaSuccess) return set_err(CHEM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&gc.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { gc.exec = nullptr; return set_err(CHEM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e)); }
+    gc.key = key;
+  }
+  CK(cudaGraphLaunch(gc.exec, st));
+  return 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1254,6 +1328,8 @@ void chem_default_opts(chem_opts* o) {
   o->cells_per_cta = 0;
   o->ctas_per_sm = 0;
   o->warps_per_cell = 0;
+  o->use_graph = 0;
+  o->batch_cells = 0;
 }
 
 int chem_load_mechanism(const char* path, chem_mech** out) {
@@ -1367,6 +1443,8 @@ int chem_load_mechanism(const char* path, chem_mech** out) {
 
 void chem_free_mechanism(chem_mech* m) {
   if (!m) return;
+  if (m->graph.exec) cudaGraphExecDestroy(m->graph.exec);
+  if (m->graph.capture_stream) cudaStreamDestroy(m->graph.capture_stream);
   cudaFree(m->dbuf);
   cudaFree(m->d_totals);
   cudaFree(m->d_queue);
@@ -1415,12 +1493,12 @@ static int rates_or_jacobian(const chem_mech* mc, double p_Pa, const double* T, 
   Launch L;
   int rc = pick_launch(m, ncells, 0, 0, 0, false, L);
   if (rc) return rc;
-  if (L.G == 1)
-    rates_kernel<1><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, p_Pa * 10.0, dT, dY, ncells, df, dJ);
-  else if (L.G == 2)
-    rates_kernel<2><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, p_Pa * 10.0, dT, dY, ncells, df, dJ);
-  else
-    rates_kernel<4><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, p_Pa * 10.0, dT, dY, ncells, df, dJ);
+  switch (L.G) {
+    case 1: rates_kernel<1><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, p_Pa * 10.0, dT, dY, ncells, df, dJ); break;
+    case 2: rates_kernel<2><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, p_Pa * 10.0, dT, dY, ncells, df, dJ); break;
+    case 4: rates_kernel<4><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, p_Pa * 10.0, dT, dY, ncells, df, dJ); break;
+    default: rates_kernel<8><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, p_Pa * 10.0, dT, dY, ncells, df, dJ); break;
+  }
   CK(cudaGetLastError());
   if (!dev) {
     if (f) CK(cudaMemcpyAsync(f, df, sizeof(double) * N * ncells, cudaMemcpyDeviceToHost, st));
@@ -1482,25 +1560,20 @@ int chem_integrate(const chem_mech* mc, double p_Pa, double* T, double* Y, int64
     CK(cudaMemcpyAsync(dY, Y, sizeof(double) * nY, cudaMemcpyHostToDevice, st));
     if (h_inout) CK(cudaMemcpyAsync(dh, h_inout, sizeof(double) * nh, cudaMemcpyHostToDevice, st));
   }
-  CK(cudaMemsetAsync(m->d_totals, 0, 4 * sizeof(unsigned long long), st));
-  CK(cudaMemsetAsync(m->d_queue, 0, sizeof(int), st));
-  Launch L;
-  rc = pick_launch(m, ncells, o.warps_per_cell, o.cells_per_cta, o.ctas_per_sm, true, L);
-  if (rc) return rc;
   IntegrateArgs a;
+  std::memset(&a, 0, sizeof(a));  // padding too: the graph cache compares whole argument sets
   a.p = p_Pa * 10.0; a.dt = dt; a.rtol = rtol; a.atol = atol;
   a.T = dT; a.Y = dY; a.h_inout = dh; a.status = dstat;
   a.steps_out = m->d_steps; a.rej_out = m->d_rej;
   a.totals = m->d_totals; a.queue = m->d_queue;
-  a.ncells = ncells; a.max_steps = o.max_steps; a.use_queue = o.use_queue;
+  a.ncells = ncells; a.first = 0; a.count = ncells; a.max_steps = o.max_steps; a.use_queue = o.use_queue;
   a.mixed = o.precision == CHEM_PREC_MIXED; a.refine_sweeps = o.refine_sweeps;
-  if (L.G == 1)
-    integrate_kernel<1><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, a);
-  else if (L.G == 2)
-    integrate_kernel<2><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, a);
-  else
-    integrate_kernel<4><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, a);
-  CK(cudaGetLastError());
+  if (o.use_graph && dev) {
+    rc = launch_via_graph(m, o, a, st);
+  } else {
+    rc = enqueue_integrate(m, o, a, st);
+  }
+  if (rc) return rc;
   if (!dev) {
     CK(cudaMemcpyAsync(T, dT, sizeof(double) * ncells, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(Y, dY, sizeof(double) * K * ncells, cudaMemcpyDeviceToHost, st));
@@ -1596,14 +1669,9 @@ int chem_integrate_noalloc(const chem_mech* mc, double p_Pa, double* T, double* 
   a.steps_out = d_steps; a.rej_out = d_rej;
   a.totals = reinterpret_cast<unsigned long long*>(s + 64);
   a.queue = reinterpret_cast<int*>(s);
-  a.ncells = ncells; a.max_steps = o.max_steps; a.use_queue = o.use_queue;
+  a.ncells = ncells; a.first = 0; a.count = ncells; a.max_steps = o.max_steps; a.use_queue = o.use_queue;
   a.mixed = o.precision == CHEM_PREC_MIXED; a.refine_sweeps = o.refine_sweeps;
-  if (L.G == 1)
-    integrate_kernel<1><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, a);
-  else if (L.G == 2)
-    integrate_kernel<2><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, a);
-  else
-    integrate_kernel<4><<<L.grid, L.threads, L.smem, st>>>(m->dev, L.plan, a);
+  launch_integrate(L, st, m->dev, a);
   CK(cudaGetLastError());
   if (steps) CK(cudaMemcpyAsync(steps, d_steps, sizeof(int32_t) * ncells, cudaMemcpyDeviceToDevice, st));
   if (rejects) CK(cudaMemcpyAsync(rejects, d_rej, sizeof(int32_t) * ncells, cudaMemcpyDeviceToDevice, st));

@@ -384,3 +384,53 @@ def workload_igniting(n: int = 16384):
     T, Y = cells_uniform(105, mech.K, n, (1000.0, 1300.0))
     return dict(name=f"mech53_igniting{n}", mech=mech, p_Pa=20.0 * P_ATM_PA, T=T, Y=Y, dt=1e-4,
                 rtol=1e-6, atol=1e-10)
+
+
+def burnt_templates():
+    """Equilibrium (T, Y) states of the 100-species mechanism at 60 atm, T in [2000, 2400] K
+    (written by tests/golden/make_burnt_templates.py from the oracle's thermo)."""
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden",
+                        "burnt_templates_mech100.npz")
+    d = np.load(path)
+    return d["T"], d["Y"]
+
+
+def cells_uneven(seed: int, K: int, n: int, order: str = "shuffled"):
+    """Uneven-stiffness field: 10% igniting cells (T ~ U[900, 1200] K, two Dirichlet(1) streams
+    mixed at Z ~ U[0.4, 0.6]), 60% cold cells (T ~ U[300, 700] K, Dirichlet(1) Y), 30% burnt
+    cells (equilibrium templates).  order: "shuffled" or "blocked" (igniting, cold, burnt).
+    Returns T [n], Y [K, n], class [n] (0 igniting, 1 cold, 2 burnt)."""
+    rng = np.random.default_rng(seed)
+    n_ign = n // 10
+    n_burnt = (3 * n) // 10
+    n_cold = n - n_ign - n_burnt
+    Yf = rng.dirichlet(np.ones(K))
+    Yo = rng.dirichlet(np.ones(K))
+    Z = rng.uniform(0.4, 0.6, n_ign)
+    T_ign = rng.uniform(900.0, 1200.0, n_ign)
+    Y_ign = Yf[:, None] * Z[None, :] + Yo[:, None] * (1.0 - Z[None, :])
+    T_cold = rng.uniform(300.0, 700.0, n_cold)
+    Y_cold = rng.dirichlet(np.ones(K), size=n_cold).T
+    Tt, Yt = burnt_templates()
+    if Yt.shape[1] != K:
+        raise ValueError("burnt templates are for the 100-species mechanism")
+    pick = rng.integers(0, Tt.shape[0], n_burnt)
+    T_b, Y_b = Tt[pick], Yt[pick].T
+    T = np.concatenate([T_ign, T_cold, T_b])
+    Y = np.concatenate([Y_ign, Y_cold, Y_b], axis=1)
+    cls = np.concatenate([np.zeros(n_ign, np.int32), np.ones(n_cold, np.int32), np.full(n_burnt, 2, np.int32)])
+    if order == "shuffled":
+        perm = rng.permutation(n)
+        T, Y, cls = T[perm], Y[:, perm], cls[perm]
+    elif order != "blocked":
+        raise ValueError("order must be 'shuffled' or 'blocked'")
+    return T, np.ascontiguousarray(Y), cls
+
+
+def workload_uneven(n: int = 262144, order: str = "shuffled"):
+    """100 species / 700 reactions, uneven-stiffness field (igniting / cold / burnt), 60 atm,
+    dt 5e-6 s."""
+    mech = mechanism_100()
+    T, Y, cls = cells_uneven(103, mech.K, n, order)
+    return dict(name=f"mech100_uneven{n}_{order}", mech=mech, p_Pa=60.0 * P_ATM_PA, T=T, Y=Y, cls=cls, dt=5e-6,
+                rtol=1e-6, atol=1e-10)
