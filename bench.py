@@ -52,6 +52,13 @@ def parse_args():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--cells", type=int, default=0, help="cells per rank (0 = the full 65536-cell field)")
+    ap.add_argument("--dt", type=float, default=0.0, help="override the CFD time step (profiling small cases)")
+    ap.add_argument("--workload", choices=["shear", "uneven"], default="shear",
+                    help="shear: 53-species shear layer (the headline); uneven: 100-species igniting/cold/burnt field")
+    ap.add_argument("--order", choices=["shuffled", "blocked"], default="blocked", help="cell order of --workload uneven")
+    ap.add_argument("--batch-cells", type=int, default=0,
+                    help="also time one launch per batch of this many cells (static assignment) against the queue")
+    ap.add_argument("--autotune", action="store_true", help="pick warps/cell and cells/CTA with the autotuner first")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0 = auto)")
     return ap.parse_args()
@@ -180,7 +187,12 @@ def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
     from paper_2105_12070_gb300 import synth
-    w = synth.workload_shear_layer()
+    if args.workload == "uneven":
+        w = synth.workload_uneven(args.cells or 262144, args.order)
+    else:
+        w = synth.workload_shear_layer()
+    if args.dt > 0:
+        w["dt"] = args.dt
     if args.impl == "reference":
         return run_reference(args, w, world, rank)
 
@@ -204,7 +216,12 @@ def main():
     status = torch.zeros(n_total, dtype=torch.int32, device="cuda")
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     prec = chem.CHEM_PREC_MIXED if args.precision == "mixed" else chem.CHEM_PREC_FP64
-    opts = chem.default_opts(precision=prec)
+    if args.autotune:
+        from paper_2105_12070_gb300 import autotune
+        opts = autotune.autotune(mech, w["p_Pa"], w["T"], w["Y"], w["dt"], precision=prec)
+    else:
+        opts = chem.default_opts(precision=prec)
+    opts.use_graph = 1
     stream = torch.cuda.current_stream()
 
     def one_step(timed: bool):
@@ -249,15 +266,17 @@ def main():
     cells = n_total * world * args.steps
     value = cells / (kern_ms / 1e3)
     e2e_value = cells / (e2e_ms / 1e3)
-    flops, per = algorithmic_flops(steps_np, rej_np)
+    flops, per = algorithmic_flops(steps_np, rej_np) if mech.K == 53 else (float("nan"), {"per_attempt": None,
+                                                                                      "per_accepted": None})
     achieved = flops / (kern_ms / 1e3 / args.steps) / 1e12  # TFLOP/s, one launch
     peak = fp64_peak_tflops()
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": kern_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == chem.CHEM_PREC_FP64 else "f64+f32", "data": "synthetic",
-        "config": {"workload": w["name"], "cells": n_total, "species": 53, "reactions": 325, "dt_s": w["dt"],
-                   "p_atm": 40.0, "rtol": w["rtol"], "atol": w["atol"], "precision": args.precision,
+        "config": {"workload": w["name"], "cells": n_total, "species": mech.K, "reactions": mech.R, "dt_s": w["dt"],
+                   "p_atm": w["p_Pa"] / 101325.0, "rtol": w["rtol"], "atol": w["atol"], "precision": args.precision,
+                   "warps_per_cell": opts.warps_per_cell, "cells_per_cta": opts.cells_per_cta, "cuda_graph": True,
                    "scheduling": "persistent kernel + device work queue", "l2": "flushed between steps (256 MiB write)",
                    "start": "cold (every step from the initial field)"},
         "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": int(T_host.numel() * 8 + Y_host.numel() * 8),
@@ -271,6 +290,21 @@ def main():
         "steps_per_cell": {"mean": float(steps_np.mean()), "max": int(steps_np.max()),
                            "rejects_mean": float(rej_np.mean())},
     }
+    if args.batch_cells > 0:
+        # one launch per batch of consecutive cells, static assignment inside each launch
+        bopts = chem.default_opts(precision=prec, use_queue=0, batch_cells=args.batch_cells,
+                                  warps_per_cell=opts.warps_per_cell, cells_per_cta=opts.cells_per_cta)
+        T.copy_(T_host)
+        Y.copy_(Y_host)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        chem.chem_integrate(mech, w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], status=status, opts=bopts)
+        e1.record(stream)
+        e1.synchronize()
+        bms = e0.elapsed_time(e1)
+        line["batched_launches"] = {"batch_cells": args.batch_cells, "ms_per_step": bms,
+                                    "value": n_total / (bms / 1e3), "queue_speedup": bms / (kern_ms / args.steps)}
     if rank == 0 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample or max(4 * cores, 32))

@@ -1239,12 +1239,21 @@ void launch_integrate(const Launch& L, cudaStream_t st, const DevMech& d, const 
   }
 }
 
-// Launch shape: G warps per cell (default 2 for mechanisms with >= 32 species, else 1), as many
-// cells per CTA as the shared memory allows (at most 8 warps per CTA, 15 named barriers), one
-// persistent CTA wave.
+// Launch shape: G warps per cell, as many cells per CTA as the shared memory allows (at most 8
+// warps per CTA, 15 named barriers), one persistent CTA wave.
 int pick_launch(const chem_mech* m, int64_t ncells, int want_G, int want_cpc, int want_ctas_per_sm, bool integ,
                 Launch& L) {
-  int G = want_G > 0 ? want_G : (m->host.K >= 32 ? 2 : 1);
+  int G = want_G;
+  if (G <= 0) {
+    // automatic: about 8 warps per SM -- G = 8 / (cells that fit), a power of two in 1..8, and
+    // at least 2 warps per cell from 32 species up
+    const size_t per_cell2 = (size_t)make_plan(m->host.K, m->host.R, m->dev.n_pd, 2).total * sizeof(double);
+    const int fit = (int)std::max<size_t>(1, m->max_smem / per_cell2);
+    G = 1;
+    while (G < 8 && G * fit < 8) G *= 2;
+    if (m->host.K >= 32 && G < 2) G = 2;
+    if (m->host.K < 32 && fit >= 8) G = 1;
+  }
   if (G != 1 && G != 2 && G != 4 && G != 8) return set_err(CHEM_EINVAL, "warps_per_cell must be 1, 2, 4 or 8");
   L.G = G;
   L.plan = make_plan(m->host.K, m->host.R, m->dev.n_pd, G);
