@@ -13,6 +13,9 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   jacobian     -- complex-step derivative of rates to 1e-12 row-normwise, central differences
   integrate    -- Rosenbrock order conditions and L-stability from the coefficient table,
                   closed-form A=B and A->B->C solutions, observed convergence order
+  replay / TLM -- replay of the recorded steps equals the adaptive run bit for bit; the dual-number
+                  tangent-linear result equals central differences of the replay (state and ln A
+                  directions) and the ln k / initial-state derivatives of the Bateman solution
 """
 from __future__ import annotations
 
@@ -69,6 +72,10 @@ def _load():
                                              ctypes.c_int, ctypes.c_int]
             lib.oracle_ros_coefficients.argtypes = [_dp]
             lib.oracle_opcount.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _dp, _lp]
+            lib.oracle_integrate_record.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, ctypes.c_double,
+                                                    ctypes.c_double, ctypes.c_double, _dp, ctypes.c_int, _ip]
+            lib.oracle_replay.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, ctypes.c_int, _dp, _dp, _dp,
+                                          _dp, _dp]
             _lib = lib
     return _lib
 
@@ -156,6 +163,32 @@ class OracleMechanism:
                                    _p(h_inout), _p(status, _ip), _p(steps, _ip), _p(rej, _ip), int(max_steps),
                                    int(nthreads))
         return T, Y, status, steps, rej
+
+    def integrate_record(self, p_Pa: float, phi, dt: float, rtol: float = 1e-6, atol: float = 1e-10,
+                         max_hs: int = 100000):
+        """One cell, phi = [T, Y_1..Y_{K-1}]: returns (phi_final, accepted step sizes, status)."""
+        phi = _f64(phi).copy()
+        hs = np.zeros(max_hs)
+        n = ctypes.c_int32()
+        st = self._lib.oracle_integrate_record(self._h, float(p_Pa), _p(phi), float(dt), float(rtol), float(atol),
+                                               _p(hs), max_hs, ctypes.byref(n))
+        return phi, hs[:n.value].copy(), st
+
+    def replay(self, p_Pa: float, phi, hs, dphi=None, dlnA=None, lnA_shift=None):
+        """Replays accepted steps hs from phi (with ln A_r + lnA_shift[r]); with dphi / dlnA also
+        returns the tangent-linear derivative of the final state along that direction (reaction
+        arrays in file order)."""
+        phi = _f64(phi)
+        hs = _f64(hs)
+        out = np.zeros(self.N)
+        dout = np.zeros(self.N) if (dphi is not None or dlnA is not None) else None
+        rc = self._lib.oracle_replay(self._h, float(p_Pa), _p(phi), _p(hs), int(hs.shape[0]),
+                                     _p(_f64(lnA_shift)) if lnA_shift is not None else None,
+                                     _p(_f64(dphi)) if dphi is not None else None,
+                                     _p(_f64(dlnA)) if dlnA is not None else None, _p(out), _p(dout))
+        if rc != 0:
+            raise RuntimeError("oracle replay hit a singular iteration matrix")
+        return (out, dout) if dout is not None else out
 
     def opcount(self, p_Pa: float, T: float, Y):
         Y = _f64(Y)

@@ -165,6 +165,25 @@ inline Cnt exp(Cnt a) { g_ops.exp++; return Cnt(std::exp(a.v)); }
 inline Cnt log(Cnt a) { g_ops.log++; return Cnt(std::log(a.v)); }
 inline double re(const Cnt& x) { return x.v; }
 
+// Forward-mode dual number (value, derivative along one direction) for the tangent-linear
+// (forward sensitivity) runs.
+struct Dual {
+  double v, d;
+  Dual(double x = 0.0, double dx = 0.0) : v(x), d(dx) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) { return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
+inline Dual& operator*=(Dual& a, Dual b) { a = a * b; return a; }
+inline Dual& operator/=(Dual& a, Dual b) { a = a / b; return a; }
+inline Dual exp(Dual a) { const double e = std::exp(a.v); return Dual(e, a.d * e); }
+inline Dual log(Dual a) { return Dual(std::log(a.v), a.d / a.v); }
+inline double re(const Dual& x) { return x.v; }
+
 using std::exp;
 using std::log;
 
@@ -243,7 +262,7 @@ static void troe_F(const Reaction& x, const S& T, const S& Pr, S& F, S& dlog10F_
 }
 
 template <class S>
-static void rates(const Mech& m, double p, const S* phi, S* f, RateState<S>& st) {
+static void rates(const Mech& m, double p, const S* phi, S* f, RateState<S>& st, const S* lnA_shift = nullptr) {
   const int K = m.K, R = m.R;
   st.T = phi[0];
   st.Y.resize(K);
@@ -266,7 +285,9 @@ static void rates(const Mech& m, double p, const S* phi, S* f, RateState<S>& st)
   st.k0.assign(R, S(0.0)); st.kinf.assign(R, S(0.0));
   for (int r = 0; r < R; ++r) {
     const Reaction& x = m.rx[r];
-    S kf = exp(S(std::log(x.A)) + S(x.b) * lnT - S(x.Ea / kRc) * invT);
+    S lnA = S(std::log(x.A));
+    if (lnA_shift) lnA = lnA + lnA_shift[r];  // perturbation of ln A_r (sensitivity runs)
+    S kf = exp(lnA + S(x.b) * lnT - S(x.Ea / kRc) * invT);
     S M = S(0.0);
     if (x.type >= 1) {
       for (int k = 0; k < K; ++k) M += S(x.eff[k]) * st.C[k];
@@ -326,10 +347,10 @@ static void rates(const Mech& m, double p, const S* phi, S* f, RateState<S>& st)
 //   d cp/dY_i = cp_i/W_i - cp_K/W_K (molar cp_k),  d cp/dT = sum_k Y_k (d cp_k/dT)/W_k
 
 template <class S>
-static void jacobian(const Mech& m, double p, const S* phi, S* f, S* J) {
+static void jacobian(const Mech& m, double p, const S* phi, S* f, S* J, const S* lnA_shift = nullptr) {
   const int K = m.K, R = m.R, N = K, d = K - 1;
   RateState<S> st;
-  rates(m, p, phi, f, st);
+  rates(m, p, phi, f, st, lnA_shift);
   const S T = st.T, invT = S(1.0) / T;
   std::vector<S> dlnrho_dY(K - 1);
   for (int i = 0; i < K - 1; ++i) dlnrho_dY[i] = -st.Wbar * (S(1.0) / S(m.W[i]) - S(1.0) / S(m.W[d]));
@@ -541,7 +562,7 @@ struct CellStats {
 // 0.2.  The last step is clipped so that t reaches dt exactly.  The cold-start step is
 // 0.01 dt; a positive h_inout overrides it (carry-over of the chemistry sub-step, Sec. 2.3).
 static int integrate_cell(const Mech& m, double p, double* phi, double dt, double rtol, double atol, double* h_io,
-                          int max_steps, CellStats& cs) {
+                          int max_steps, CellStats& cs, std::vector<double>* h_record = nullptr) {
   const int N = m.K;
   if (!(std::isfinite(phi[0]) && phi[0] > 0.0)) return kBadInput;
   for (int i = 1; i < N; ++i)
@@ -610,6 +631,7 @@ static int integrate_cell(const Mech& m, double p, double* phi, double dt, doubl
     }
     double fac;
     if (std::isfinite(errn) && errn <= 1.0) {
+      if (h_record) h_record->push_back(h);
       t = (h >= dt - t) ? dt : t + h;
       y = ynew;
       cs.steps++;
@@ -631,6 +653,45 @@ static int integrate_cell(const Mech& m, double p, double* phi, double dt, doubl
   for (int i = 0; i < N; ++i) phi[i] = y[i];
   if (h_io) *h_io = h_next_unclipped;
   return status;
+}
+
+// One Rosenbrock step of size h from y (no error control): the same classical-form formulas as
+// integrate_cell, templated so that the dual-number instance gives the tangent-linear step
+// (forward sensitivities through the discrete method with the step size frozen).
+template <class S>
+static bool ros_step(const Mech& m, double p, std::vector<S>& y, double h, const S* lnA_shift) {
+  const int N = m.K;
+  Ros4 c;
+  std::vector<S> f0(N), fi(N), J((size_t)N * N), A((size_t)N * N), yi(N), g(N), rhs(N);
+  std::vector<std::vector<S>> k(4, std::vector<S>(N));
+  std::vector<int> piv(N);
+  jacobian(m, p, y.data(), f0.data(), J.data(), lnA_shift);
+  for (size_t e = 0; e < (size_t)N * N; ++e) A[e] = -S(c.gamma * h) * J[e];
+  for (int i = 0; i < N; ++i) A[(size_t)i * N + i] += S(1.0);
+  if (!lu_factor(N, A.data(), piv.data())) return false;
+  for (int s = 0; s < 4; ++s) {
+    for (int i = 0; i < N; ++i) {
+      yi[i] = y[i];
+      g[i] = S(0.0);
+      for (int j = 0; j < s; ++j) { yi[i] += S(c.alpha[s][j]) * k[j][i]; g[i] += S(c.gam[s][j]) * k[j][i]; }
+    }
+    if (s == 0) {
+      fi = f0;
+    } else {
+      RateState<S> st;
+      rates(m, p, yi.data(), fi.data(), st, lnA_shift);
+    }
+    for (int i = 0; i < N; ++i) {
+      S jg = S(0.0);
+      for (int j = 0; j < N; ++j) jg += J[(size_t)i * N + j] * g[j];
+      rhs[i] = S(h) * fi[i] + S(h) * jg;
+    }
+    lu_solve(N, A.data(), piv.data(), rhs.data());
+    k[s] = rhs;
+  }
+  for (int i = 0; i < N; ++i)
+    for (int s = 0; s < 4; ++s) y[i] += S(c.b[s]) * k[s][i];
+  return true;
 }
 
 }  // namespace oracle
@@ -789,6 +850,44 @@ int oracle_integrate(void* h, double p_Pa, int64_t n, double* T, double* Y, doub
   for (int t = 1; t < nthreads; ++t) pool.emplace_back(work);
   work();
   for (auto& th : pool) th.join();
+  return 0;
+}
+
+// Integrate one cell and return the sizes of its accepted steps (hs[max_hs], *n_hs), for
+// replaying the same discrete map.  phi_io = [T, Y_1..Y_{K-1}] in/out.  Returns the status.
+int oracle_integrate_record(void* h, double p_Pa, double* phi_io, double dt, double rtol, double atol, double* hs,
+                            int max_hs, int* n_hs) {
+  Mech* m = static_cast<Mech*>(h);
+  std::vector<double> rec;
+  CellStats cs;
+  int st = integrate_cell(*m, p_Pa * 10.0, phi_io, dt, rtol, atol, nullptr, 100000, cs, &rec);
+  *n_hs = (int)rec.size();
+  for (int i = 0; i < (int)rec.size() && i < max_hs; ++i) hs[i] = rec[i];
+  return st;
+}
+
+// Replay the accepted steps hs[0..n) from phi (N) without error control: phi_out = the final
+// state, with ln A_r shifted by lnA_shift[r] (R, file order; may be NULL).  With dphi (N) and/or
+// dlnA (R) non-NULL, also the tangent-linear result dphi_out = d phi_out along (dphi, dlnA)
+// (dual numbers through the same discrete steps).
+int oracle_replay(void* h, double p_Pa, const double* phi, const double* hs, int n, const double* lnA_shift,
+                  const double* dphi, const double* dlnA, double* phi_out, double* dphi_out) {
+  Mech* m = static_cast<Mech*>(h);
+  const int N = m->K;
+  const double p = p_Pa * 10.0;
+  if (!dphi && !dlnA) {
+    std::vector<double> y(phi, phi + N);
+    for (int i = 0; i < n; ++i)
+      if (!ros_step<double>(*m, p, y, hs[i], lnA_shift)) return 1;
+    for (int i = 0; i < N; ++i) phi_out[i] = y[i];
+    return 0;
+  }
+  std::vector<Dual> y(N), shift(m->R);
+  for (int i = 0; i < N; ++i) y[i] = Dual(phi[i], dphi ? dphi[i] : 0.0);
+  for (int r = 0; r < m->R; ++r) shift[r] = Dual(lnA_shift ? lnA_shift[r] : 0.0, dlnA ? dlnA[r] : 0.0);
+  for (int i = 0; i < n; ++i)
+    if (!ros_step<Dual>(*m, p, y, hs[i], shift.data())) return 1;
+  for (int i = 0; i < N; ++i) { phi_out[i] = y[i].v; if (dphi_out) dphi_out[i] = y[i].d; }
   return 0;
 }
 
