@@ -44,6 +44,8 @@ extern "C" {
 #define CHEM_CELL_MAX_STEPS 1    /* step-attempt limit reached before t = dt */
 #define CHEM_CELL_H_UNDERFLOW 2  /* proposed step fell below 1e-14 dt */
 #define CHEM_CELL_BAD_INPUT 3    /* non-finite input or T <= 0; state left unchanged */
+#define CHEM_CELL_RECORD_FULL 4  /* chem_integrate_record: more accepted steps than max_steps_rec;
+                                    the cell stops at its last recorded step */
 
 /* precision of the linear solves inside the Rosenbrock stages */
 #define CHEM_PREC_FP64 0   /* FP64 LU and substitutions */
@@ -132,6 +134,45 @@ int chem_integrate(const chem_mech* mech, double p_Pa, double* T, double* Y, int
 int chem_integrate_noalloc(const chem_mech* mech, double p_Pa, double* T, double* Y, int64_t ncells, double dt,
                            double rtol, double atol, double* h_inout, int32_t* status, int32_t* steps,
                            int32_t* rejects, const chem_opts* opts, chem_stats* stats, void* stream);
+
+/* Sensitivities (the discrete adjoint of the integrator).  The paper integrates forward only;
+ * these entry points differentiate its solve: the map (phi_0, ln A) -> phi(dt) computed by the
+ * accepted Rosenbrock steps of Sec. 2.3 (Eq. 2), with the step sizes frozen at the values the
+ * controller chose.  A is the pre-exponential factor of the forward rate constant of each
+ * reaction (of k_inf for fall-off reactions), in the file's reaction order.
+ *
+ * chem_integrate_record: chem_integrate in FP64 that also writes a checkpoint of every accepted
+ * step: rec[(c * max_steps_rec + n) * (N + 1) + i] = phi_n[i] (the state the step starts from,
+ * i < N) and [.. + N] = h_n (its size), N = K, for n < nsteps[c].  rec holds ncells *
+ * max_steps_rec * (N + 1) doubles; a cell that needs more accepted steps ends with status
+ * CHEM_CELL_RECORD_FULL.  opts->precision must be CHEM_PREC_FP64.  Device arrays only
+ * (CHEM_EINVAL otherwise); status and nsteps must not be NULL. */
+int chem_integrate_record(const chem_mech* mech, double p_Pa, double* T, double* Y, int64_t ncells, double dt,
+                          double rtol, double atol, double* h_inout, int32_t* status, double* rec,
+                          int32_t max_steps_rec, int32_t* nsteps, const chem_opts* opts, chem_stats* stats,
+                          void* stream);
+
+/* chem_adjoint: the reverse sweep over the checkpoints of chem_integrate_record (same mechanism
+ * handle, pressure and ln A values).  Given gT[c] = dL/dT(dt) and gY[k * ncells + c] =
+ * dL/dY_k(dt) of a scalar L of the final states (all K species; Y_K(dt) = 1 - sum of the others,
+ * so its gradient enters as dL/dY_k - dL/dY_K), it writes
+ *   gT0[c] = dL/dT(0), gY0[k * ncells + c] = dL/dY_k(0) for k < K-1 and 0 for k = K-1 (the
+ *     solve never reads the input Y_K),
+ *   g_lnA[r] = sum over cells of dL/d ln A_r (NULL: not computed), summed in a fixed order,
+ *   g_lnA_cells[c * R + r] = the same per cell (NULL: not kept).
+ * Per accepted step it recomputes the stages from the checkpoint, applies the transposed stage
+ * solves with the same LU, the transposed Jacobians at the stage states, and the derivatives of
+ * J and of f with respect to phi and ln A along the stage increments (dual numbers, exact up to
+ * rounding).  A cell whose status is not CHEM_CELL_OK gets NaN gradients (and NaN in g_lnA).
+ * Device arrays only; asynchronous on `stream`. */
+int chem_adjoint(const chem_mech* mech, double p_Pa, int64_t ncells, const double* rec, int32_t max_steps_rec,
+                 const int32_t* nsteps, const int32_t* status, const double* gT, const double* gY, double* gT0,
+                 double* gY0, double* g_lnA, double* g_lnA_cells, void* stream);
+
+/* ln A_r of every reaction (file order, R values, host arrays): read the mechanism's values, or
+ * replace them (the device tables are updated synchronously; later calls use the new values). */
+int chem_get_lnA(const chem_mech* mech, double* lnA);
+int chem_set_lnA(chem_mech* mech, const double* lnA);
 
 /* Per-cell counters of the last chem_integrate on this mechanism handle, copied to the
  * caller's arrays (device or host, ncells entries each, either may be NULL).  Valid until the

@@ -76,6 +76,7 @@ def _load():
                                                     ctypes.c_double, ctypes.c_double, _dp, ctypes.c_int, _ip]
             lib.oracle_replay.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, ctypes.c_int, _dp, _dp, _dp,
                                           _dp, _dp]
+            lib.oracle_jacobian_dir.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
             _lib = lib
     return _lib
 
@@ -189,6 +190,16 @@ class OracleMechanism:
         if rc != 0:
             raise RuntimeError("oracle replay hit a singular iteration matrix")
         return (out, dout) if dout is not None else out
+
+    def jacobian_dir(self, p_Pa: float, phi, dphi=None, dlnA=None):
+        """At one state phi: (f, J, df, dJ), df and dJ the derivatives of f and J along
+        (dphi, dlnA) (dual numbers; reaction arrays in file order)."""
+        phi = _f64(phi)
+        f, df = np.zeros(self.N), np.zeros(self.N)
+        J, dJ = np.zeros((self.N, self.N)), np.zeros((self.N, self.N))
+        self._lib.oracle_jacobian_dir(self._h, float(p_Pa), _p(phi), _p(_f64(dphi)) if dphi is not None else None,
+                                      _p(_f64(dlnA)) if dlnA is not None else None, _p(f), _p(J), _p(df), _p(dJ))
+        return f, J, df, dJ
 
     def opcount(self, p_Pa: float, T: float, Y):
         Y = _f64(Y)

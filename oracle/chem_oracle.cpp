@@ -802,6 +802,21 @@ int oracle_jacobian(void* h, double p_Pa, int64_t n, const double* T, const doub
   return 0;
 }
 
+// Directional derivatives at one state phi (N): f and J (row i = d f_i / d phi) together with
+// their derivatives df, dJ along (dphi, dlnA) (dual numbers; either direction may be NULL).
+int oracle_jacobian_dir(void* h, double p_Pa, const double* phi, const double* dphi, const double* dlnA, double* f,
+                        double* J, double* df, double* dJ) {
+  Mech* m = static_cast<Mech*>(h);
+  const int N = m->K;
+  std::vector<Dual> x(N), fo(N), Jd((size_t)N * N), shift(m->R);
+  for (int i = 0; i < N; ++i) x[i] = Dual(phi[i], dphi ? dphi[i] : 0.0);
+  for (int r = 0; r < m->R; ++r) shift[r] = Dual(0.0, dlnA ? dlnA[r] : 0.0);
+  jacobian(*m, p_Pa * 10.0, x.data(), fo.data(), Jd.data(), shift.data());
+  for (int i = 0; i < N; ++i) { f[i] = fo[i].v; df[i] = fo[i].d; }
+  for (size_t e = 0; e < (size_t)N * N; ++e) { J[e] = Jd[e].v; dJ[e] = Jd[e].d; }
+  return 0;
+}
+
 // Complex-step Jacobian of f at one state: Jcs[N][N] with Jcs[i][j] = Im f_i(phi + i h e_j)/h.
 int oracle_jacobian_cs(void* h, double p_Pa, double T, const double* Y, double step, double* Jcs) {
   Mech* m = static_cast<Mech*>(h);

@@ -1,8 +1,10 @@
 """Builds libchemgpu.so (the C-ABI library of include/chemgpu.h) in-tree for sm_103a.
 
-Two translation units compiled in parallel with nvcc, linked as one shared library:
+Three translation units compiled in parallel with nvcc, linked as one shared library:
   csrc/mech_tables.cpp  -- mechanism reader and table layout (host)
-  csrc/chem_kernels.cu  -- kernels, launchers and the extern "C" entry points
+  csrc/chem_kernels.cu  -- forward kernels, launchers and the extern "C" entry points
+  csrc/adjoint.cu       -- the discrete-adjoint kernels (reverse sweep)
+(csrc/cell_device.cuh holds the device code both kernel files share.)
 """
 from __future__ import annotations
 
@@ -16,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libchemgpu.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["mech_tables.cpp", "chem_kernels.cu"]
+SOURCES = ["mech_tables.cpp", "chem_kernels.cu", "adjoint.cu"]
 
 
 def _nvcc():

@@ -20,7 +20,8 @@ _lib = None
 
 CHEM_PREC_FP64 = 0
 CHEM_PREC_MIXED = 1
-CELL_STATUS = {0: "ok", 1: "max_steps", 2: "h_underflow", 3: "bad_input"}
+CELL_STATUS = {0: "ok", 1: "max_steps", 2: "h_underflow", 3: "bad_input", 4: "record_full"}
+CHEM_CELL_RECORD_FULL = 4
 
 
 class ChemOpts(ctypes.Structure):
@@ -69,9 +70,14 @@ def load_library(build_if_missing: bool = True):
         lib.chem_debug_exp.argtypes = [vp, vp, i64, vp]
         lib.chem_integrate_noalloc.argtypes = [vp, dp, vp, vp, i64, dp, dp, dp, vp, vp, vp, vp,
                                                ctypes.POINTER(ChemOpts), ctypes.POINTER(ChemStats), vp]
+        lib.chem_integrate_record.argtypes = [vp, dp, vp, vp, i64, dp, dp, dp, vp, vp, vp, ctypes.c_int32, vp,
+                                              ctypes.POINTER(ChemOpts), ctypes.POINTER(ChemStats), vp]
+        lib.chem_adjoint.argtypes = [vp, dp, i64, vp, ctypes.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.chem_get_lnA.argtypes = [vp, vp]
+        lib.chem_set_lnA.argtypes = [vp, vp]
         for name in ("chem_load_mechanism", "chem_mech_dims", "chem_rates", "chem_jacobian", "chem_integrate",
                      "chem_last_cell_counters", "chem_probe_fp64_peak", "chem_integrate_noalloc",
-                     "chem_debug_exp"):
+                     "chem_debug_exp", "chem_integrate_record", "chem_adjoint", "chem_get_lnA", "chem_set_lnA"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -215,6 +221,71 @@ def chem_integrate_noalloc(mech: Mechanism, p_Pa: float, T, Y, dt: float, rtol: 
                                             ph, ps, pst, prj, ctypes.byref(opts) if opts is not None else None,
                                             ctypes.byref(st) if st is not None else None, _stream(stream, dT)))
     return st
+
+
+def chem_integrate_record(mech: Mechanism, p_Pa: float, T, Y, dt: float, rec, nsteps, status, rtol: float = 1e-6,
+                          atol: float = 1e-10, h_inout=None, opts: ChemOpts | None = None, want_stats: bool = False,
+                          stream=None):
+    """chem_integrate (FP64) that also checkpoints every accepted step for chem_adjoint: device
+    tensors only; rec is (ncells, max_steps_rec, N + 1) float64, nsteps and status (ncells,) int32."""
+    n = _cells(mech, T, Y)
+    if rec.dim() != 3 or rec.shape[0] != n or rec.shape[2] != mech.N + 1:
+        raise ValueError(f"rec must have shape (ncells={n}, max_steps_rec, N+1={mech.N + 1})")
+    pT, dT = _ptr(T, np.float64)
+    pY, _ = _ptr(Y, np.float64)
+    ph, _ = _ptr(h_inout, np.float64)
+    ps, _ = _ptr(status, np.int32)
+    pr, _ = _ptr(rec, np.float64)
+    pn, _ = _ptr(nsteps, np.int32)
+    st = ChemStats() if want_stats else None
+    _check(mech._lib.chem_integrate_record(mech.handle, float(p_Pa), pT, pY, n, float(dt), float(rtol), float(atol),
+                                           ph, ps, pr, int(rec.shape[1]), pn,
+                                           ctypes.byref(opts) if opts is not None else None,
+                                           ctypes.byref(st) if st is not None else None, _stream(stream, dT)))
+    return st
+
+
+def chem_adjoint(mech: Mechanism, p_Pa: float, rec, nsteps, status, gT, gY, gT0, gY0, g_lnA=None, g_lnA_cells=None,
+                 stream=None):
+    """Reverse sweep over the checkpoints of chem_integrate_record: from dL/dT(dt) = gT (ncells,) and
+    dL/dY(dt) = gY (K, ncells) writes dL/dT(0) to gT0, dL/dY(0) to gY0, and (if given) the sum over
+    cells of dL/d ln A to g_lnA (R,) and its per-cell terms to g_lnA_cells (ncells, R), reactions
+    in file order.  Device tensors only."""
+    n = int(gT.shape[0])
+    if tuple(gY.shape) != (mech.K, n) or tuple(gY0.shape) != (mech.K, n) or tuple(gT0.shape) != (n,):
+        raise ValueError("gradient arrays must be (ncells,) and (K, ncells)")
+    if rec.dim() != 3 or rec.shape[0] != n or rec.shape[2] != mech.N + 1:
+        raise ValueError(f"rec must have shape (ncells={n}, max_steps_rec, N+1={mech.N + 1})")
+    if g_lnA is not None and tuple(g_lnA.shape) != (mech.R,):
+        raise ValueError(f"g_lnA must have shape (R={mech.R},)")
+    if g_lnA_cells is not None and tuple(g_lnA_cells.shape) != (n, mech.R):
+        raise ValueError(f"g_lnA_cells must have shape (ncells={n}, R={mech.R})")
+    ptrs = [_ptr(x, np.float64)[0] for x in (rec,)]
+    pn, dev = _ptr(nsteps, np.int32)
+    ps, _ = _ptr(status, np.int32)
+    pgT, _ = _ptr(gT, np.float64)
+    pgY, _ = _ptr(gY, np.float64)
+    pgT0, _ = _ptr(gT0, np.float64)
+    pgY0, _ = _ptr(gY0, np.float64)
+    pgA, _ = _ptr(g_lnA, np.float64)
+    pgC, _ = _ptr(g_lnA_cells, np.float64)
+    _check(mech._lib.chem_adjoint(mech.handle, float(p_Pa), n, ptrs[0], int(rec.shape[1]), pn, ps, pgT, pgY, pgT0,
+                                  pgY0, pgA, pgC, _stream(stream, dev)))
+
+
+def chem_get_lnA(mech: Mechanism) -> np.ndarray:
+    """ln A_r of every reaction (file order)."""
+    out = np.zeros(mech.R)
+    _check(mech._lib.chem_get_lnA(mech.handle, ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def chem_set_lnA(mech: Mechanism, lnA):
+    """Replace ln A_r of every reaction (file order, R values); synchronises the device."""
+    a = np.ascontiguousarray(np.asarray(lnA, dtype=np.float64))
+    if a.shape != (mech.R,):
+        raise ValueError(f"lnA must have shape (R={mech.R},)")
+    _check(mech._lib.chem_set_lnA(mech.handle, ctypes.c_void_p(a.ctypes.data)))
 
 
 def chem_last_cell_counters(mech: Mechanism, steps, rejects, stream=None):

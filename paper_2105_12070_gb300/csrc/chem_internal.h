@@ -87,6 +87,7 @@ struct DevMech {
   const int* pr_row;
   const int* pr_rows;
   int n_pairs, n_prows;
+  const int* order;  // device reaction index -> file reaction index
 };
 
 }  // namespace chemgpu

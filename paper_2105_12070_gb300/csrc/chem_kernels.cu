@@ -1,11 +1,12 @@
-// chemgpu kernels and C ABI (see include/chemgpu.h).
+// chemgpu kernels and C ABI (see include/chemgpu.h): the forward integrator, the one-shot
+// rate and Jacobian kernels, and the host side (mechanism upload, launch shapes, CUDA graphs).
 //
-// GPU design (GB300, sm_103a).  One warp integrates one cell at a time; a CTA holds several
-// independent cell warps; a persistent grid pulls cells from a device work queue (one atomic
-// per cell), so that cells of very different stiffness balance across SMs -- the on-device
-// counterpart of the paper's MPI load balancing (Sec. 2.2).  Each warp keeps its cell's whole
-// working set in shared memory: the dense Jacobian (Sec. 2.3), the iteration matrix and its LU
-// factors, the stage vectors and the per-reaction scratch.
+// GPU design (GB300, sm_103a).  A group of G warps integrates one cell at a time; a CTA holds
+// several independent cell groups; a persistent grid pulls cells from a device work queue (one
+// atomic per cell), so that cells of very different stiffness balance across SMs -- the
+// on-device counterpart of the paper's MPI load balancing (Sec. 2.2).  Each group keeps its
+// cell's whole working set in shared memory: the dense Jacobian (Sec. 2.3), the iteration
+// matrix and its LU factors, the stage vectors and the per-reaction scratch.
 //
 // FP64 is the bottleneck on this part (measured ~0.5 T DFMA/s, 1/74 of FP32), and an FP64 warp
 // instruction costs the same with 1 or 32 active lanes, so the work is laid out to keep all
@@ -21,738 +22,11 @@
 #include <vector>
 
 #include "../../include/chemgpu.h"
+#include "adjoint.h"
+#include "cell_device.cuh"
 #include "chem_internal.h"
 
-using namespace chemgpu;
-
 namespace {
-
-constexpr double kRu = 8.314462618e7;  // erg/(mol K)
-constexpr double kPatm = 1.01325e6;    // dyn/cm^2
-constexpr double kLnPatmRu = -4.4074185890025275;  // ln(Patm / Ru), Patm/Ru in mol K / cm^3
-constexpr unsigned kFull = 0xffffffffu;
-
-// ------------------------------------------------------------------------------------------
-// Rosenbrock method (transformed form of Hairer & Wanner IV.7): with W = I/(gamma h) - J,
-//   W u_i = f(y + sum_j a_ij u_j) + sum_j (c_ij / h) u_j,  y_new = y + sum m_i u_i,
-//   error = sum e_i u_i.  4 stages, order 4(3), L-stable; a_4j = a_3j so stage 4 reuses the
-// rate evaluation of stage 3.  (gamma is the root near 0.5728 of the order-4 L-stability
-// polynomial; the classical coefficients alpha_21 = 2 gamma, alpha_3 = 0.65, b_3 = 0,
-// beta_43 = -0.23 and R_hat(inf) = 1/2 fix the rest through the order conditions.)
-__constant__ double c_gamma = 0.5728160624821348554080014;
-__constant__ double c_a21 = 2.0;
-__constant__ double c_a31 = 1.860719413892191158443;
-__constant__ double c_a32 = 0.2350527673509341985179;
-__constant__ double c_c21 = -7.137649921358897064356;
-__constant__ double c_c31 = 2.514641112124939467064;
-__constant__ double c_c32 = 0.6358184234567149330241;
-__constant__ double c_c41 = -2.12191165112287042299;
-__constant__ double c_c42 = -0.3261607745737058543668;
-__constant__ double c_c43 = -0.7009668191330486406986;
-__constant__ double c_m[4] = {2.258943599044704060723, 0.294864173772259595933, 0.4414500735399588815281,
-                              1.099433447424383102325};
-__constant__ double c_e[4] = {-0.2561963508749719744122, -0.07156405471952786716643,
-                              -0.09930846885424478507654, -0.9949360460805926517866};
-
-// ------------------------------------------------------------------------------------------
-// Cell groups.  G warps (32 G threads) cooperate on one cell; several groups share a CTA and
-// synchronise with their own named barrier (ids 1..15).  Reductions go through a small
-// per-group scratch in a fixed order, so results do not depend on scheduling.
-
-template <int G>
-struct Grp {
-  static constexpr int NT = 32 * G;
-  int t;        // thread index in the group
-  int gid;      // group index in the CTA
-  double* red;  // 6 G doubles of reduction scratch
-  mutable int parity;
-
-  __device__ int lane() const { return t & 31; }
-  __device__ int warp() const { return t >> 5; }
-  __device__ void sync() const {
-    if (G == 1) {
-      __syncwarp();
-    } else {
-      asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(NT) : "memory");
-    }
-  }
-  __device__ double sum(double v) const {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    if (G == 1) return v;
-    double* r = red + (parity & 1) * 3 * G;  // alternate halves: no reader of the previous
-    parity++;                                // call can still be reading this one
-    if (lane() == 0) r[warp()] = v;
-    sync();
-    double s = r[0];
-#pragma unroll
-    for (int i = 1; i < G; ++i) s += r[i];
-    return s;
-  }
-  // two sums at once (one exchange)
-  __device__ void sum2(double& a, double& b) const {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(kFull, a, o);
-      b += __shfl_xor_sync(kFull, b, o);
-    }
-    if (G == 1) return;
-    double* r = red + (parity & 1) * 3 * G;
-    parity++;
-    if (lane() == 0) { r[2 * warp()] = a; r[2 * warp() + 1] = b; }
-    sync();
-    a = r[0];
-    b = r[1];
-#pragma unroll
-    for (int i = 1; i < G; ++i) { a += r[2 * i]; b += r[2 * i + 1]; }
-  }
-  // max that propagates NaN (a NaN error norm must reject the step)
-  __device__ static double nanmax(double a, double b) { return (a > b || a != a) ? a : b; }
-  __device__ double max_nan(double v) const {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(kFull, v, o));
-    if (G == 1) return v;
-    double* r = red + (parity & 1) * 3 * G;
-    parity++;
-    if (lane() == 0) r[warp()] = v;
-    sync();
-    double s = r[0];
-#pragma unroll
-    for (int i = 1; i < G; ++i) s = nanmax(s, r[i]);
-    return s;
-  }
-  // argmax of key (ties to the lowest index) over the group, carrying a value along
-  __device__ void argmax(long long& key, int& idx, double& val) const {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const long long ok = __shfl_xor_sync(kFull, key, o);
-      const int oi = __shfl_xor_sync(kFull, idx, o);
-      const double ov = __shfl_xor_sync(kFull, val, o);
-      if (ok > key || (ok == key && oi < idx)) { key = ok; idx = oi; val = ov; }
-    }
-    if (G == 1) return;
-    double* r = red + (parity & 1) * 3 * G;
-    parity++;
-    if (lane() == 0) {
-      r[3 * warp()] = __longlong_as_double(key);
-      r[3 * warp() + 1] = __int2double_rn(idx);
-      r[3 * warp() + 2] = val;
-    }
-    sync();
-    key = __double_as_longlong(r[0]);
-    idx = (int)r[1];
-    val = r[2];
-#pragma unroll
-    for (int i = 1; i < G; ++i) {
-      const long long ok = __double_as_longlong(r[3 * i]);
-      const int oi = (int)r[3 * i + 1];
-      if (ok > key || (ok == key && oi < idx)) { key = ok; idx = oi; val = r[3 * i + 2]; }
-    }
-  }
-};
-
-// ------------------------------------------------------------------------------------------
-// Per-cell shared-memory plan (doubles).
-
-struct Plan {
-  int N, K, R, n_pd, G;
-  int SA;  // size of each of the two matrix buffers: max(N*N, 8*R)
-  int off_A, off_B, off_vec, off_sp, off_q, off_M, off_piv, off_red, total;
-};
-
-__host__ __device__ inline int round2(int x) { return (x + 1) & ~1; }
-
-__host__ __device__ inline Plan make_plan(int K, int R, int n_pd, int G) {
-  Plan p;
-  p.N = K; p.K = K; p.R = R; p.n_pd = n_pd; p.G = G;
-  p.SA = round2(max(K * K, 8 * R));
-  p.off_A = 0;
-  p.off_B = p.SA;
-  p.off_vec = 2 * p.SA;
-  // vectors: y, ynew, f0, fs, u0..u3, err, invdiag, rhs, res, (er, ec as ints), (FP32 inverse
-  // pivots)  (14 x N); the Jacobian's temporaries zc, dwT, rowA, rowB, ccol reuse u0..u3, err
-  p.off_sp = p.off_vec + 14 * round2(K);
-  // species: C, hRT, cpR, gRT, omega, dcpR  (6 x K)
-  p.off_q = p.off_sp + 6 * round2(K);
-  p.off_M = p.off_q + round2(R);
-  p.off_piv = p.off_M + round2(max(n_pd, 1));
-  p.off_red = p.off_piv + round2(K + 2);  // pivots and the composed permutation (ints)
-  p.total = p.off_red + 6 * G + 2;  // reduction scratch + queue slot
-  p.total = round2(p.total);
-  return p;
-}
-
-struct CellMem {
-  double *A, *B;
-  double *y, *ynew, *f0, *fs, *u[4], *err, *invdiag, *zc, *dwT, *rowA, *rowB, *ccol, *rhs, *res;
-  int *er, *ec;
-  float* invd32;
-  double *C, *hRT, *cpR, *gRT, *omega, *dcpR;
-  double *q, *M, *red;
-  int* piv;
-  int* perm;
-  int* slot;
-};
-
-__device__ inline CellMem carve(double* base, const Plan& p) {
-  CellMem w;
-  w.A = base + p.off_A;
-  w.B = base + p.off_B;
-  const int n = round2(p.K);
-  double* v = base + p.off_vec;
-  w.y = v; w.ynew = v + n; w.f0 = v + 2 * n; w.fs = v + 3 * n;
-  for (int i = 0; i < 4; ++i) w.u[i] = v + (4 + i) * n;
-  w.err = v + 8 * n; w.invdiag = v + 9 * n;
-  w.zc = w.u[0]; w.dwT = w.u[1]; w.rowA = w.u[2]; w.rowB = w.u[3]; w.ccol = w.err;
-  w.rhs = v + 10 * n; w.res = v + 11 * n;
-  w.er = reinterpret_cast<int*>(v + 12 * n);
-  w.ec = w.er + n;
-  w.invd32 = reinterpret_cast<float*>(v + 13 * n);
-  double* s = base + p.off_sp;
-  w.C = s; w.hRT = s + n; w.cpR = s + 2 * n; w.gRT = s + 3 * n; w.omega = s + 4 * n; w.dcpR = s + 5 * n;
-  w.q = base + p.off_q;
-  w.M = base + p.off_M;
-  w.piv = reinterpret_cast<int*>(base + p.off_piv);
-  w.perm = w.piv + p.K + 2;
-  w.red = base + p.off_red;
-  w.slot = reinterpret_cast<int*>(base + p.off_red + 6 * p.G);
-  return w;
-}
-
-// ------------------------------------------------------------------------------------------
-// Thermochemistry and rates (Eq. 1).  Scalars of the cell state, identical in every thread.
-
-struct CellScalars {
-  double T, invT, lnT, rho, inv_rho, Wbar, cp, dcp_dT, fT;
-};
-
-// exp(x) for the rate constants: Tang's table-driven method (P. T. P. Tang, "Table-driven
-// implementation of the exponential function in IEEE floating-point arithmetic", ACM TOMS 15,
-// 1989): x = (32 m + j) ln2/32 + r with |r| <= ln2/64, exp(x) = 2^m 2^(j/32) (1 + p(r)), p the
-// degree-6 Taylor polynomial (truncation below 2e-18), 2^(j/32) as a double-double.  About 12
-// FP64 operations instead of a library call's ~17; |x| >= 708 and NaN go to exp().
-__device__ const double c_exp2_j32[64] = {
-    0x1.0000000000000p+0, 0x0.0p+0,
-    0x1.059b0d3158574p+0, 0x1.d73e2a475b465p-55,
-    0x1.0b5586cf9890fp+0, 0x1.8a62e4adc610bp-54,
-    0x1.11301d0125b51p+0, -0x1.6c51039449b3ap-54,
-    0x1.172b83c7d517bp+0, -0x1.19041b9d78a76p-55,
-    0x1.1d4873168b9aap+0, 0x1.e016e00a2643cp-54,
-    0x1.2387a6e756238p+0, 0x1.9b07eb6c70573p-54,
-    0x1.29e9df51fdee1p+0, 0x1.612e8afad1255p-55,
-    0x1.306fe0a31b715p+0, 0x1.6f46ad23182e4p-55,
-    0x1.371a7373aa9cbp+0, -0x1.63aeabf42eae2p-54,
-    0x1.3dea64c123422p+0, 0x1.ada0911f09ebcp-55,
-    0x1.44e086061892dp+0, 0x1.89b7a04ef80d0p-59,
-    0x1.4bfdad5362a27p+0, 0x1.d4397afec42e2p-56,
-    0x1.5342b569d4f82p+0, -0x1.07abe1db13cadp-55,
-    0x1.5ab07dd485429p+0, 0x1.6324c054647adp-54,
-    0x1.6247eb03a5585p+0, -0x1.383c17e40b497p-54,
-    0x1.6a09e667f3bcdp+0, -0x1.bdd3413b26456p-54,
-    0x1.71f75e8ec5f74p+0, -0x1.16e4786887a99p-55,
-    0x1.7a11473eb0187p+0, -0x1.41577ee04992fp-55,
-    0x1.82589994cce13p+0, -0x1.d4c1dd41532d8p-54,
-    0x1.8ace5422aa0dbp+0, 0x1.6e9f156864b27p-54,
-    0x1.93737b0cdc5e5p+0, -0x1.75fc781b57ebcp-57,
-    0x1.9c49182a3f090p+0, 0x1.c7c46b071f2bep-56,
-    0x1.a5503b23e255dp+0, -0x1.d2f6edb8d41e1p-54,
-    0x1.ae89f995ad3adp+0, 0x1.7a1cd345dcc81p-54,
-    0x1.b7f76f2fb5e47p+0, -0x1.5584f7e54ac3bp-56,
-    0x1.c199bdd85529cp+0, 0x1.11065895048ddp-55,
-    0x1.cb720dcef9069p+0, 0x1.503cbd1e949dbp-56,
-    0x1.d5818dcfba487p+0, 0x1.2ed02d75b3707p-55,
-    0x1.dfc97337b9b5fp+0, -0x1.1a5cd4f184b5cp-54,
-    0x1.ea4afa2a490dap+0, -0x1.e9c23179c2893p-54,
-    0x1.f50765b6e4540p+0, 0x1.9d3e12dd8a18bp-54};
-
-__device__ inline double exp_fast(double x) {
-  if (!(fabs(x) < 708.0)) return exp(x);
-  const double shifter = 0x1.8p52;  // adding it rounds x 32/ln2 to an integer in the low bits
-  const double t = fma(x, 0x1.71547652b82fep+5, shifter);
-  const int k = (int)__double2loint(t);
-  const double kd = t - shifter;
-  double r = fma(-kd, 0x1.62e42fefa39efp-6, x);  // ln2/32, high part
-  r = fma(-kd, 0x1.abc9e3b39803fp-61, r);        // ln2/32, low part
-  double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
-  q = fma(r, q, 1.0 / 24.0);
-  q = fma(r, q, 1.0 / 6.0);
-  q = fma(r, q, 0.5);
-  const double p = fma(r * r, q, r);
-  const int j = k & 31;
-  const double th = __ldg(&c_exp2_j32[2 * j]), tl = __ldg(&c_exp2_j32[2 * j + 1]);
-  const double res = fma(th, p, tl) + th;
-  // times 2^(k >> 5): add to the exponent field (the result stays normal for |x| < 708)
-  return __longlong_as_double(__double_as_longlong(res) + ((long long)(k >> 5) << 52));
-}
-
-// 2^k as a double (|k| < 1000), exact.
-__device__ inline double pow2(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
-
-// Binary exponent of |a| (the biased exponent field; 0 for zero and subnormals).
-__device__ inline int exp_field(double a) { return (int)((__double_as_longlong(a) >> 52) & 0x7ff); }
-
-// NASA-7: cp/R, h/RT, s/R and d(cp/R)/dT.
-__device__ inline void nasa7(const double* a, double T, double invT, double lnT, double& cpR, double& hRT,
-                             double& sR, double& dcpR) {
-  cpR = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
-  hRT = a[0] + T * (a[1] * 0.5 + T * (a[2] * (1.0 / 3.0) + T * (a[3] * 0.25 + T * a[4] * 0.2))) + a[5] * invT;
-  sR = a[0] * lnT + T * (a[1] + T * (a[2] * 0.5 + T * (a[3] * (1.0 / 3.0) + T * a[4] * 0.25))) + a[6];
-  dcpR = a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]));
-}
-
-// Troe broadening: F and d log10 F / d log10 Pr; with jac also d ln F / dT at fixed Pr.
-__device__ inline void troe(const double* fo, double T, double invT, double Pr, double& F, double& dlF,
-                            double& dlnF_dT, bool jac) {
-  const double a = fo[3], T3 = fo[4], T1 = fo[5], T2 = fo[6];
-  const double e3 = exp_fast(-T / T3), e1 = exp_fast(-T / T1), e2 = exp_fast(-T2 * invT);
-  const double Fcent = (1.0 - a) * e3 + a * e1 + e2;
-  const double L = log10(Fcent);
-  const double c = -0.4 - 0.67 * L, n = 0.75 - 1.27 * L;
-  const double x = log10(Pr);
-  const double den = n - 0.14 * (x + c);
-  const double f1 = (x + c) / den;
-  const double g = 1.0 + f1 * f1;
-  F = exp_fast(2.302585092994045684 * (L / g));
-  dlF = -2.0 * L * f1 / (g * g) * (n / (den * den));
-  dlnF_dT = 0.0;
-  if (jac) {
-    const double dFc = -(1.0 - a) / T3 * e3 - a / T1 * e1 + T2 * invT * invT * e2;
-    const double dL = dFc / (Fcent * 2.302585092994045684);
-    const double df1_dL = (-0.67 * den - (x + c) * (-1.27 + 0.14 * 0.67)) / (den * den);
-    const double dlog10F_dL = 1.0 / g - L * 2.0 * f1 / (g * g) * df1_dL;
-    dlnF_dT = 2.302585092994045684 * dlog10F_dL * dL;
-  }
-}
-
-// Evaluates f(y) into f[0..N).  With jac, also leaves per-reaction derivative data in
-// scr[r*8 + 0..7] = {dq/dC at the 4 distinct slot species, phi (coefficient of the
-// efficiencies), sum_j dq/dC_j C_j, dq/dT at fixed C, reaction enthalpy (erg/mol)} and the
-// species production rates in w.omega.
-template <int G>
-__device__ CellScalars cell_rates(const DevMech& m, const Grp<G>& g, double p, const double* y, double* f,
-                                  const CellMem& w, double* scr, bool jac) {
-  constexpr int NT = Grp<G>::NT;
-  const int K = m.K, d = K - 1;
-  CellScalars s;
-  s.T = y[0];
-  s.invT = 1.0 / s.T;
-  s.lnT = log(s.T);
-  // mass fractions, mean molar mass, density, concentrations, thermo
-  double ysum = 0.0, yw = 0.0;
-  for (int k = g.t; k < d; k += NT) {
-    const double Yk = y[1 + k];
-    ysum += Yk;
-    yw += Yk * m.sp[k * kSpDoubles + 1];
-  }
-  g.sum2(ysum, yw);
-  const double Yd = 1.0 - ysum;
-  yw += Yd * m.sp[d * kSpDoubles + 1];
-  s.Wbar = 1.0 / yw;
-  s.rho = p * s.Wbar / (kRu * s.T);
-  s.inv_rho = yw * kRu * s.T / p;
-  double cp = 0.0, dcp = 0.0;
-  for (int k = g.t; k < K; k += NT) {
-    const double* sp = m.sp + k * kSpDoubles;
-    const double Yk = (k < d) ? y[1 + k] : Yd;
-    w.C[k] = s.rho * Yk * sp[1];
-    const double* a = (s.T <= sp[2]) ? sp + 3 : sp + 10;
-    double cpR, hRT, sR, dcpR;
-    nasa7(a, s.T, s.invT, s.lnT, cpR, hRT, sR, dcpR);
-    w.cpR[k] = cpR;
-    w.hRT[k] = hRT;
-    w.gRT[k] = hRT - sR;
-    w.dcpR[k] = dcpR;
-    cp += Yk * cpR * sp[1];
-    dcp += Yk * dcpR * sp[1];
-  }
-  g.sum2(cp, dcp);
-  s.cp = cp * kRu;
-  s.dcp_dT = dcp * kRu;
-  g.sync();
-  // third-body concentrations [M]_r = sum_k eff_rk C_k of the pressure-dependent reactions
-  for (int r = g.t; r < m.n_pd; r += NT) {
-    const double* e = m.eff + (size_t)r * K;
-    double a0 = 0.0, a1 = 0.0;
-    int k = 0;
-    for (; k + 1 < K; k += 2) {
-      a0 = fma(e[k], w.C[k], a0);
-      a1 = fma(e[k + 1], w.C[k + 1], a1);
-    }
-    if (k < K) a0 = fma(e[k], w.C[k], a0);
-    w.M[r] = a0 + a1;
-  }
-  g.sync();
-  const double ln_patm_rut = kLnPatmRu - s.lnT;  // ln(Patm / (Ru T))
-  for (int r = g.t; r < m.R; r += NT) {
-    const int* ii = m.rxi + r * kRxInts;
-    const double* rd = m.rxd + r * kRxDoubles;
-    const int a0 = ii[0], a1 = ii[1], p0 = ii[2], p1 = ii[3];
-    const double Ca0 = w.C[a0], Ca1 = (a1 >= 0) ? w.C[a1] : 1.0;
-    const double Cp0 = w.C[p0], Cp1 = (p1 >= 0) ? w.C[p1] : 1.0;
-    const double pf = Ca0 * Ca1, pr = Cp0 * Cp1;
-    double kf = exp_fast(fma(rd[1], s.lnT, rd[0]) - rd[2] * s.invT);
-    double dG = w.gRT[p0] - w.gRT[a0];
-    if (p1 >= 0) dG += w.gRT[p1];
-    if (a1 >= 0) dG -= w.gRT[a1];
-    const int dnu = m.dnu[r];
-    // 1/Kc = exp(sum nu g/RT - dnu ln(Patm/(Ru T)))
-    const double invKc = exp_fast(dG - dnu * ln_patm_rut);
-    double mfac = 1.0, Mr = 0.0;
-    double Pr = 0.0, F = 1.0, dlF = 0.0, dlnF_dT = 0.0, k0 = 0.0;
-    const bool pd = r < m.n_pd;
-    const bool fo = r < m.n_fo;
-    const double* fop = nullptr;
-    if (pd) Mr = w.M[r];
-    if (fo) {
-      fop = m.fo + (size_t)r * kFoDoubles;
-      k0 = exp_fast(fma(fop[1], s.lnT, fop[0]) - fop[2] * s.invT);
-      Pr = k0 * Mr / kf;
-      if (fop[7] != 0.0) troe(fop, s.T, s.invT, Pr, F, dlF, dlnF_dT, jac);
-      kf = kf * Pr / (1.0 + Pr) * F;
-    } else if (pd) {
-      mfac = Mr;
-    }
-    const double kr = kf * invKc;
-    const double q = mfac * (kf * pf - kr * pr);
-    w.q[r] = q;
-    if (jac) {
-      double* o = scr + (size_t)r * 8;
-      double dH = w.hRT[p0] - w.hRT[a0];
-      if (p1 >= 0) dH += w.hRT[p1];
-      if (a1 >= 0) dH -= w.hRT[a1];
-      const double dlnKc_dT = (dH - dnu) * s.invT;
-      const double dlnkinf = (rd[1] + rd[2] * s.invT) * s.invT;
-      double phi = 0.0, dlnk = dlnkinf;
-      if (fo) {
-        const double inv1p = 1.0 / (1.0 + Pr);
-        const double dk_dM = k0 * F * inv1p * (inv1p + dlF);
-        phi = dk_dM * (pf - invKc * pr);
-        const double dlnk0 = (fop[1] + fop[2] * s.invT) * s.invT;
-        dlnk = dlnkinf + (inv1p + dlF) * (dlnk0 - dlnkinf) + dlnF_dT;
-      } else if (pd) {
-        phi = kf * pf - kr * pr;
-      }
-      const double dqdT = mfac * (kf * dlnk * pf - kr * (dlnk - dlnKc_dT) * pr);
-      double DC = phi * Mr;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = ii[4 + u];
-        double D = 0.0;
-        if (j >= 0) {
-          const double dpf = (a0 == j ? Ca1 : 0.0) + (a1 == j ? Ca0 : 0.0);
-          const double dpr = (p0 == j ? Cp1 : 0.0) + (p1 == j ? Cp0 : 0.0);
-          D = mfac * (kf * dpf - kr * dpr);
-          DC = fma(D, w.C[j], DC);
-        }
-        o[u] = D;
-      }
-      o[4] = phi;
-      o[5] = DC;
-      o[6] = dqdT;
-      o[7] = dH * kRu * s.T;
-    }
-  }
-  g.sync();
-  // species production rates and the source term
-  double Qp = 0.0;
-  for (int k = g.t; k < K; k += NT) {
-    double om = 0.0;
-    for (int e = m.sr_ptr[k]; e < m.sr_ptr[k + 1]; ++e) om = fma(m.sr_nu[e], w.q[m.sr_idx[e]], om);
-    w.omega[k] = om;
-    Qp = fma(w.hRT[k], om, Qp);
-    if (k < d) f[1 + k] = m.sp[k * kSpDoubles] * om * s.inv_rho;
-  }
-  const double Q = g.sum(Qp) * kRu * s.T;
-  s.fT = -Q * s.inv_rho / s.cp;
-  if (g.t == 0) f[0] = s.fT;
-  g.sync();
-  return s;
-}
-
-// Assemble the analytical Jacobian (Sec. 2.3) at the state of the preceding cell_rates(jac)
-// call.  J (overwritten) holds the per-reaction data on entry, Z is N*N scratch, J receives
-// -d f / d phi (stored negated, so that W = I/(gamma h) - J is a copy plus the diagonal).  Chain rule through C_j = rho Y_j / W_j, rho = p Wbar/(Ru T), Y_K = 1 - sum Y_i;
-// Z rows k < K-1 hold d omega_k / dC, row K-1 holds d Q / dC (Q = sum_k H_k omega_k).
-template <int G>
-__device__ void cell_jacobian(const DevMech& m, const Grp<G>& g, const CellScalars& s, const double* f,
-                              const CellMem& w, double* J, double* Z) {
-  constexpr int NT = Grp<G>::NT;
-  const int K = m.K, N = K, d = K - 1;
-  const double* scr = J;
-  for (int e = g.t; e < N * N; e += NT) Z[e] = 0.0;
-  g.sync();
-  // mass-action part: one thread per receiving Z entry sums its contributions (a fixed plan
-  // built with the mechanism; no two threads write the same entry, no atomics)
-  for (int e = g.t; e < m.zg_entries; e += NT) {
-    double acc = 0.0;
-    const int cb = m.zg_ptr[e], ce = m.zg_ptr[e + 1];
-    for (int c = cb; c < ce; ++c) acc = fma(m.zg_coef[c], scr[m.zg_src[c]], acc);
-    Z[m.zg_dst[e]] = acc;
-  }
-  g.sync();
-  // efficiency part of the pressure-dependent reactions: Z[k][j] += sum_r v_kr eff_rj over the
-  // (row k, reaction r) pairs, v_kr = nu_kr phi_r.  The coefficients go to the stage-vector area
-  // first (free while the Jacobian is built).
-  double* v = w.u[0];
-  for (int c = g.t; c < m.n_pairs; c += NT) v[c] = m.pr_nu[c] * scr[(size_t)m.pr_pd[c] * 8 + 4];
-  g.sync();
-  {
-    const float invK = 1.0f / (float)K;
-    const int items = m.n_prows * K;
-    for (int x = g.t; x < items; x += NT) {
-      const int ri = (int)(((float)x + 0.5f) * invK), j = x - ri * K;
-      const int row = m.pr_rows[ri];
-      double acc = 0.0;
-      for (int c = m.pr_ptr[row]; c < m.pr_ptr[row + 1]; ++c) acc = fma(v[c], m.eff[(size_t)m.pr_pd[c] * K + j], acc);
-      Z[row * N + j] += acc;
-    }
-  }
-  g.sync();
-  // per-species gathers of sum_j dq/dC_j C_j and dq/dT; enthalpy weights of the species rows
-  const double invWd = m.sp[d * kSpDoubles + 1];
-  const double RuT = kRu * s.T;
-  double* wq = w.res;
-  for (int k = g.t; k < d; k += NT) {
-    double zc = 0.0, dw = 0.0;
-    for (int e = m.sr_ptr[k]; e < m.sr_ptr[k + 1]; ++e) {
-      const double nu = m.sr_nu[e];
-      const int r = m.sr_idx[e];
-      zc = fma(nu, scr[(size_t)r * 8 + 5], zc);
-      dw = fma(nu, scr[(size_t)r * 8 + 6], dw);
-    }
-    w.zc[k] = zc;
-    w.dwT[k] = dw;
-    // mass conservation (sum_k W_k omega_k = 0) gives omega_K = -sum_{k<K} (W_k/W_K) omega_k, so
-    // Q = sum_k H_k omega_k = sum_{k<K} (H_k - H_K W_k/W_K) omega_k: the enthalpy row is a
-    // weighted sum of the species rows
-    wq[k] = RuT * (w.hRT[k] - w.hRT[d] * m.sp[k * kSpDoubles] * invWd);
-  }
-  g.sync();
-  // enthalpy row Z_Q[j] = sum_k wq_k Z[k][j] (stored in row K-1), with sum_j Z_Q[j] C_j and
-  // dQ/dT|_C = sum_k wq_k dw_k/dT|_C
-  double zqc = 0.0, dqt = 0.0, cpw = 0.0;
-  for (int j = g.t; j < K; j += NT) {
-    double a0 = 0.0, a1 = 0.0;
-    int k = 0;
-    for (; k + 1 < d; k += 2) {
-      a0 = fma(wq[k], Z[k * N + j], a0);
-      a1 = fma(wq[k + 1], Z[(k + 1) * N + j], a1);
-    }
-    if (k < d) a0 = fma(wq[k], Z[k * N + j], a0);
-    const double zq = a0 + a1;
-    Z[d * N + j] = zq;
-    zqc = fma(zq, w.C[j], zqc);
-    cpw = fma(w.cpR[j], w.omega[j], cpw);
-  }
-  for (int k = g.t; k < d; k += NT) dqt = fma(wq[k], w.dwT[k], dqt);
-  g.sum2(zqc, dqt);
-  cpw = g.sum(cpw) * kRu;
-  g.sync();
-  // per-row and per-column factors
-  for (int k = g.t; k < d; k += NT) {
-    const double Wk = m.sp[k * kSpDoubles];
-    w.rowA[k] = Wk * invWd * Z[k * N + d];
-    w.rowB[k] = Wk * s.inv_rho * (w.zc[k] - w.omega[k]);
-    w.ccol[k] = -s.Wbar * (m.sp[k * kSpDoubles + 1] - invWd);
-  }
-  g.sync();
-  const double inv_rhocp = s.inv_rho / s.cp;
-  const double inv_cp = 1.0 / s.cp;
-  const double fT = s.fT;
-  // temperature row and column, then the species block (J now overwrites the scratch)
-  const double ZQd = Z[d * N + d];
-  const double cpd = w.cpR[d] * invWd;
-  for (int i = g.t; i < d; i += NT) {
-    const double ci = w.ccol[i];
-    const double invWi = m.sp[i * kSpDoubles + 1];
-    const double dQdY = s.rho * (invWi * Z[d * N + i] - invWd * ZQd) + zqc * ci;
-    const double dcpdY = (w.cpR[i] * invWi - cpd) * kRu;
-    J[1 + i] = fma(dQdY, inv_rhocp, fT * (ci + dcpdY * inv_cp));
-    const double Wk = m.sp[i * kSpDoubles];
-    J[(1 + i) * N] = -(Wk * s.inv_rho * (w.dwT[i] - w.zc[i] * s.invT) + f[1 + i] * s.invT);
-  }
-  if (g.t == 0) J[0] = (cpw + dqt - zqc * s.invT) * inv_rhocp + fT * (-s.invT + s.dcp_dT * inv_cp);
-  const int nb = d * d;
-  const float inv_d = 1.0f / (float)d;
-  for (int e = g.t; e < nb; e += NT) {
-    const int k = (int)(((float)e + 0.5f) * inv_d), i = e - k * d;
-    const double Wk = m.sp[k * kSpDoubles];
-    const double invWi = m.sp[i * kSpDoubles + 1];
-    J[(1 + k) * N + 1 + i] = fma(-w.rowB[k], w.ccol[i], fma(-Wk * invWi, Z[k * N + i], w.rowA[k]));
-  }
-  g.sync();
-}
-
-// ------------------------------------------------------------------------------------------
-// Dense LU with partial pivoting (row interchanges, ties to the lowest row), in place, and the
-// substitutions that use it (Sec. 2.3: dense LU + back substitution).  Returns false on an
-// exactly zero pivot.
-
-// |a| as an ordered integer key (bit pattern of a non-negative float / double)
-__device__ inline long long abs_key(double a) { return __double_as_longlong(fabs(a)); }
-__device__ inline long long abs_key(float a) { return (long long)__float_as_int(fabsf(a)); }
-
-template <int G, typename S>
-__device__ bool cell_lu(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* invdiag) {
-  constexpr int NT = Grp<G>::NT;
-  bool ok = true;
-  for (int k = 0; k < N; ++k) {
-    // pivot: largest |a_ik|, compared as the bit patterns of |a| (monotone for non-negative)
-    long long best = -1;
-    int bi = N;
-    double bv = 0.0;
-    for (int i = k + g.t; i < N; i += NT) {
-      const S a = A[i * N + k];
-      const long long v = abs_key(a);
-      if (v > best) { best = v; bi = i; bv = (double)a; }
-    }
-    g.argmax(best, bi, bv);
-    // one thread takes the reciprocal of the pivot while the others swap the rows
-    if (g.t == 0) {
-      piv[k] = bi;
-      invdiag[k] = S(1) / S(bv);
-    }
-    if (best <= 0) ok = false;  // zero column: singular
-    if (bi != k) {
-      for (int j = g.t; j < N; j += NT) {
-        const S t = A[k * N + j];
-        A[k * N + j] = A[bi * N + j];
-        A[bi * N + j] = t;
-      }
-    }
-    g.sync();
-    const S inv = invdiag[k];
-    for (int i = k + 1 + g.t; i < N; i += NT) A[i * N + k] *= inv;
-    g.sync();
-    const int mm = N - k - 1;
-    const int tot = mm * mm;
-    if (tot > 0) {
-      const float inv_m = 1.0f / (float)mm;
-      S* Ak = A + (size_t)(k + 1) * N + k;  // column k of the trailing rows
-      const S* U = A + (size_t)k * N + k + 1;  // pivot row right of the diagonal
-      S* T0 = A + (size_t)(k + 1) * N + k + 1;
-      // four independent updates per thread and iteration (loads first, then the FMAs)
-      int e = g.t;
-      for (; e + 3 * NT < tot; e += 4 * NT) {
-        int ii[4], jj[4];
-        S l[4], u[4], a[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int x = e + q * NT;
-          ii[q] = (int)(((float)x + 0.5f) * inv_m);
-          jj[q] = x - ii[q] * mm;
-          l[q] = Ak[ii[q] * N];
-          u[q] = U[jj[q]];
-          a[q] = T0[ii[q] * N + jj[q]];
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) T0[ii[q] * N + jj[q]] = fma(-l[q], u[q], a[q]);
-      }
-      for (; e < tot; e += NT) {
-        const int i = (int)(((float)e + 0.5f) * inv_m);
-        const int j = e - i * mm;
-        T0[i * N + j] = fma(-Ak[i * N], U[j], T0[i * N + j]);
-      }
-    }
-    g.sync();
-  }
-  // compose the row interchanges: row i of the factors is row perm[i] of the original matrix
-  if (g.t == 0) {
-    for (int i = 0; i < N; ++i) perm[i] = i;
-    for (int k = 0; k < N; ++k) {
-      const int p = piv[k];
-      const int t = perm[k];
-      perm[k] = perm[p];
-      perm[p] = t;
-    }
-  }
-  g.sync();
-  return ok;
-}
-
-// x <- A^-1 x with the factors of cell_lu, by one warp with x in registers: lane l holds rows
-// l, l+32, .. (S slots, N <= 32 S), so a column step is a shuffle and one FMA per slot that
-// still holds rows below (forward) or above (backward) the column, without shared-memory round
-// trips or barriers.  The slot loops are unrolled over compile-time bounds so that no FMA is
-// issued for a slot with no active row.  perm is the composed row permutation of the LU.
-// T is double (FP64 factors) or float (mixed precision; then b is scaled by 2^-er on entry and
-// the result by 2^-ec on exit, see form_and_factor32).
-template <int S, typename T>
-__device__ void warp_lu_solve_s(const T* A, int N, const int* perm, const T* invdiag, const int* er, const int* ec,
-                                const double* b, double* x) {
-  const int lane = threadIdx.x & 31;
-  T xr[S];
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const int i = lane + 32 * s;
-    T v = T(0);
-    if (i < N) {
-      const int pi = perm[i];
-      v = er ? (T)(b[pi] * pow2(-er[pi])) : (T)b[pi];
-    }
-    xr[s] = v;
-  }
-  __syncwarp();
-  // forward substitution with the unit lower factor: column j in slot jb updates slots >= jb
-#pragma unroll
-  for (int jb = 0; jb < S; ++jb) {
-    const int jend = min(32 * jb + 32, N - 1);
-    for (int j = 32 * jb; j < jend; ++j) {
-      const T xj = __shfl_sync(kFull, xr[jb], j & 31);
-#pragma unroll
-      for (int s = jb; s < S; ++s) {
-        const int i = lane + 32 * s;
-        if (i > j && i < N) xr[s] = fma(-A[i * N + j], xj, xr[s]);
-      }
-    }
-  }
-  // back substitution with the upper factor: column j in slot jb updates slots <= jb
-#pragma unroll
-  for (int jb = S - 1; jb >= 0; --jb) {
-    for (int j = min(32 * jb + 31, N - 1); j >= 32 * jb; --j) {
-      const T xj = __shfl_sync(kFull, xr[jb], j & 31) * invdiag[j];
-      if (lane == (j & 31)) xr[jb] = xj;
-#pragma unroll
-      for (int s = 0; s <= jb; ++s) {
-        const int i = lane + 32 * s;
-        if (i < j) xr[s] = fma(-A[i * N + j], xj, xr[s]);
-      }
-    }
-  }
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const int i = lane + 32 * s;
-    if (i < N) x[i] = ec ? (double)xr[s] * pow2(-ec[i]) : (double)xr[s];
-  }
-  __syncwarp();
-}
-
-template <typename T>
-__device__ void warp_lu_solve_any(const T* A, int N, const int* perm, const T* invdiag, const int* er, const int* ec,
-                                  const double* b, double* x) {
-  if (N <= 32) warp_lu_solve_s<1, T>(A, N, perm, invdiag, er, ec, b, x);
-  else if (N <= 64) warp_lu_solve_s<2, T>(A, N, perm, invdiag, er, ec, b, x);
-  else if (N <= 96) warp_lu_solve_s<3, T>(A, N, perm, invdiag, er, ec, b, x);
-  else warp_lu_solve_s<4, T>(A, N, perm, invdiag, er, ec, b, x);
-}
-
-__device__ void warp_lu_solve(const double* A, int N, const int* perm, const double* invdiag, double* x) {
-  warp_lu_solve_any<double>(A, N, perm, invdiag, nullptr, nullptr, x, x);
-}
-
-// Mixed precision: x <- W^-1 b through the FP32 factors of the equilibrated matrix
-// S = D_r W D_c (D_r, D_c powers of two): z = D_r b, S v = z in FP32, x = D_c v.
-__device__ void warp_lu_solve32(const float* A, int N, const int* perm, const float* invdiag, const int* er,
-                                const int* ec, const double* b, double* x) {
-  warp_lu_solve_any<float>(A, N, perm, invdiag, er, ec, b, x);
-}
-
-template <int G>
-__device__ inline void cell_solve(const Grp<G>& g, const double* A, int N, const int* perm, const double* invdiag,
-                                  double* x) {
-  if (g.warp() == 0) warp_lu_solve(A, N, perm, invdiag, x);
-  g.sync();
-}
 
 // ------------------------------------------------------------------------------------------
 // Optional per-phase cycle counters (compile with -DCHEM_PHASE_TIMERS): thread 0 of each cell
@@ -793,6 +67,8 @@ struct IntegrateArgs {
   int use_queue;
   int mixed;          // FP32 factors + FP64-residual refinement
   int refine_sweeps;  // refinement sweeps per stage solve (mixed)
+  double* rec;        // record mode: checkpoint of every accepted step (NULL: off)
+  int rec_cap;        // checkpoints per cell
 };
 
 // ------------------------------------------------------------------------------------------
@@ -937,9 +213,9 @@ __global__ void __launch_bounds__(256, 1) integrate_kernel(DevMech m, Plan plan,
       if (h_next < 1e-14 * a.dt) { status = CHEM_CELL_H_UNDERFLOW; break; }
       PHASE_BEGIN
       if (need_jac) {
-        const CellScalars s0 = cell_rates(m, g, a.p, w.y, w.f0, w, w.A, true);
+        const CellScalars s0 = cell_rates(m, g, a.p, w.y, w.f0, eval_mem(w), w.A, true);
         PHASE_END(0);
-        cell_jacobian(m, g, s0, w.f0, w, w.A, w.B);
+        cell_jacobian(m, g, s0, w.f0, eval_mem(w), w.A, w.B);
         PHASE_END(1);
         need_jac = false;
       }
@@ -974,7 +250,7 @@ __global__ void __launch_bounds__(256, 1) integrate_kernel(DevMech m, Plan plan,
         if (conv) {
           for (int i = g.t; i < N; i += NT) w.ynew[i] = fma(c_a21, w.u[0][i], w.y[i]);
           g.sync();
-          cell_rates(m, g, a.p, w.ynew, w.fs, w, nullptr, false);
+          cell_rates(m, g, a.p, w.ynew, w.fs, eval_mem(w), (double*)nullptr, false);
           PHASE_END(4);
           for (int i = g.t; i < N; i += NT) w.rhs[i] = fma(c_c21 * invh, w.u[0][i], w.fs[i]);
           g.sync();
@@ -985,7 +261,7 @@ __global__ void __launch_bounds__(256, 1) integrate_kernel(DevMech m, Plan plan,
         if (conv) {
           for (int i = g.t; i < N; i += NT) w.ynew[i] = w.y[i] + c_a31 * w.u[0][i] + c_a32 * w.u[1][i];
           g.sync();
-          cell_rates(m, g, a.p, w.ynew, w.fs, w, nullptr, false);
+          cell_rates(m, g, a.p, w.ynew, w.fs, eval_mem(w), (double*)nullptr, false);
           PHASE_END(4);
           for (int i = g.t; i < N; i += NT)
             w.rhs[i] = w.fs[i] + invh * (c_c31 * w.u[0][i] + c_c32 * w.u[1][i]);
@@ -1031,6 +307,13 @@ __global__ void __launch_bounds__(256, 1) integrate_kernel(DevMech m, Plan plan,
       }
       double fac;
       if (err <= 1.0) {
+        if (a.rec) {
+          // checkpoint (phi_n, h_n) of the accepted step for the adjoint
+          if (nsteps >= a.rec_cap) { status = CHEM_CELL_RECORD_FULL; break; }
+          double* ck = a.rec + ((size_t)cell * a.rec_cap + nsteps) * (N + 1);
+          for (int i = g.t; i < N; i += NT) ck[i] = w.y[i];
+          if (g.t == 0) ck[N] = h;
+        }
         t = (h >= a.dt - t) ? a.dt : t + h;
         for (int i = g.t; i < N; i += NT) w.y[i] = w.ynew[i];
         g.sync();
@@ -1092,9 +375,9 @@ __global__ void __launch_bounds__(256, 1) rates_kernel(DevMech m, Plan plan, dou
     for (int i = g.t; i < N; i += NT) w.y[i] = (i == 0) ? T[cell] : Y[(size_t)(i - 1) * ncells + cell];
     g.sync();
     const bool jac = out_J != nullptr;
-    CellScalars s = cell_rates(m, g, p, w.y, w.f0, w, w.A, jac);
+    CellScalars s = cell_rates(m, g, p, w.y, w.f0, eval_mem(w), w.A, jac);
     if (jac) {
-      cell_jacobian(m, g, s, w.f0, w, w.A, w.B);
+      cell_jacobian(m, g, s, w.f0, eval_mem(w), w.A, w.B);
       double* o = out_J + (size_t)cell * N * N;
       for (int e = g.t; e < N * N; e += NT) o[e] = -w.A[e];
     }
@@ -1160,6 +443,9 @@ struct chem_mech {
   int64_t cap_cells = 0;
   void* d_stage = nullptr;  // device staging for host-pointer calls
   size_t cap_stage = 0;
+  double* d_adj_ws = nullptr;  // reverse-sweep workspace
+  size_t cap_adj_ws = 0;
+  int* d_adj_counters = nullptr;
 };
 
 namespace {
@@ -1382,6 +668,7 @@ int chem_load_mechanism(const char* path, chem_mech** out) {
   const size_t o_prn = place(std::max<size_t>(1, h.pr_nu.size()) * sizeof(double));
   const size_t o_prr = place(std::max<size_t>(1, h.pr_row.size()) * sizeof(int));
   const size_t o_prs = place(std::max<size_t>(1, h.pr_rows.size()) * sizeof(int));
+  const size_t o_ord = place(h.order.size() * sizeof(int));
   const size_t total = off;
   std::vector<char> img(total, 0);
   auto put = [&](size_t o, const void* src, size_t bytes) { if (bytes) std::memcpy(img.data() + o, src, bytes); };
@@ -1404,6 +691,7 @@ int chem_load_mechanism(const char* path, chem_mech** out) {
   put(o_prn, h.pr_nu.data(), h.pr_nu.size() * sizeof(double));
   put(o_prr, h.pr_row.data(), h.pr_row.size() * sizeof(int));
   put(o_prs, h.pr_rows.data(), h.pr_rows.size() * sizeof(int));
+  put(o_ord, h.order.data(), h.order.size() * sizeof(int));
   e = cudaMalloc(&m->dbuf, total);
   if (e == cudaSuccess) e = cudaMemcpy(m->dbuf, img.data(), total, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&m->d_totals, 4 * sizeof(unsigned long long));
@@ -1436,6 +724,7 @@ int chem_load_mechanism(const char* path, chem_mech** out) {
   d.pr_nu = reinterpret_cast<const double*>(b + o_prn);
   d.pr_row = reinterpret_cast<const int*>(b + o_prr);
   d.pr_rows = reinterpret_cast<const int*>(b + o_prs);
+  d.order = reinterpret_cast<const int*>(b + o_ord);
   d.n_pairs = (int)h.pr_pd.size();
   d.n_prows = (int)h.pr_rows.size();
   if (d.n_pairs > 8 * (((h.K + 1) / 2) * 2)) {
@@ -1460,6 +749,8 @@ void chem_free_mechanism(chem_mech* m) {
   cudaFree(m->d_steps);
   cudaFree(m->d_rej);
   cudaFree(m->d_stage);
+  cudaFree(m->d_adj_ws);
+  cudaFree(m->d_adj_counters);
   delete m;
 }
 
@@ -1529,9 +820,9 @@ int chem_jacobian(const chem_mech* m, double p_Pa, const double* T, const double
   return rates_or_jacobian(m, p_Pa, T, Y, ncells, nullptr, J, stream);
 }
 
-int chem_integrate(const chem_mech* mc, double p_Pa, double* T, double* Y, int64_t ncells, double dt, double rtol,
-                   double atol, double* h_inout, int32_t* status, const chem_opts* opts, chem_stats* stats,
-                   void* stream) {
+static int integrate_impl(const chem_mech* mc, double p_Pa, double* T, double* Y, int64_t ncells, double dt,
+                          double rtol, double atol, double* h_inout, int32_t* status, const chem_opts* opts,
+                          chem_stats* stats, void* stream, double* rec, int rec_cap) {
   chem_mech* m = const_cast<chem_mech*>(mc);
   if (ncells < 0) return set_err(CHEM_EINVAL, "chem_integrate: ncells < 0");
   if (!m || (ncells > 0 && (!T || !Y))) return set_err(CHEM_EINVAL, "chem_integrate: NULL argument");
@@ -1577,6 +868,7 @@ int chem_integrate(const chem_mech* mc, double p_Pa, double* T, double* Y, int64
   a.totals = m->d_totals; a.queue = m->d_queue;
   a.ncells = ncells; a.first = 0; a.count = ncells; a.max_steps = o.max_steps; a.use_queue = o.use_queue;
   a.mixed = o.precision == CHEM_PREC_MIXED; a.refine_sweeps = o.refine_sweeps;
+  a.rec = rec; a.rec_cap = rec_cap;
   if (o.use_graph && dev) {
     rc = launch_via_graph(m, o, a, st);
   } else {
@@ -1600,6 +892,89 @@ int chem_integrate(const chem_mech* mc, double p_Pa, double* T, double* Y, int64
   } else if (!dev) {
     CK(cudaStreamSynchronize(st));
   }
+  return CHEM_OK;
+}
+
+int chem_integrate(const chem_mech* m, double p_Pa, double* T, double* Y, int64_t ncells, double dt, double rtol,
+                   double atol, double* h_inout, int32_t* status, const chem_opts* opts, chem_stats* stats,
+                   void* stream) {
+  return integrate_impl(m, p_Pa, T, Y, ncells, dt, rtol, atol, h_inout, status, opts, stats, stream, nullptr, 0);
+}
+
+int chem_integrate_record(const chem_mech* m, double p_Pa, double* T, double* Y, int64_t ncells, double dt,
+                          double rtol, double atol, double* h_inout, int32_t* status, double* rec,
+                          int32_t max_steps_rec, int32_t* nsteps, const chem_opts* opts, chem_stats* stats,
+                          void* stream) {
+  if (!m) return set_err(CHEM_EINVAL, "chem_integrate_record: NULL mechanism");
+  if (ncells < 0) return set_err(CHEM_EINVAL, "chem_integrate_record: ncells < 0");
+  if (max_steps_rec < 1) return set_err(CHEM_EINVAL, "chem_integrate_record: max_steps_rec < 1");
+  if (opts && opts->precision != CHEM_PREC_FP64)
+    return set_err(CHEM_EINVAL, "chem_integrate_record: record mode integrates in FP64 only");
+  if (ncells == 0) {
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    return CHEM_OK;
+  }
+  if (!rec || !status || !nsteps || !T || !Y) return set_err(CHEM_EINVAL, "chem_integrate_record: NULL argument");
+  const void* arrays[6] = {T, Y, h_inout, status, rec, nsteps};
+  for (const void* ptr : arrays)
+    if (ptr && !is_device_ptr(ptr)) return set_err(CHEM_EINVAL, "chem_integrate_record: device arrays only");
+  int rc = integrate_impl(m, p_Pa, T, Y, ncells, dt, rtol, atol, h_inout, status, opts, stats, stream, rec,
+                          max_steps_rec);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(nsteps, m->d_steps, sizeof(int32_t) * ncells, cudaMemcpyDeviceToDevice,
+                     static_cast<cudaStream_t>(stream)));
+  return CHEM_OK;
+}
+
+int chem_adjoint(const chem_mech* mc, double p_Pa, int64_t ncells, const double* rec, int32_t max_steps_rec,
+                 const int32_t* nsteps, const int32_t* status, const double* gT, const double* gY, double* gT0,
+                 double* gY0, double* g_lnA, double* g_lnA_cells, void* stream) {
+  chem_mech* m = const_cast<chem_mech*>(mc);
+  if (!m) return set_err(CHEM_EINVAL, "chem_adjoint: NULL mechanism");
+  if (ncells < 0 || ncells > (int64_t)0x7fffffff) return set_err(CHEM_EINVAL, "chem_adjoint: bad ncells");
+  if (max_steps_rec < 1) return set_err(CHEM_EINVAL, "chem_adjoint: max_steps_rec < 1");
+  if (!(p_Pa > 0.0)) return set_err(CHEM_EINVAL, "chem_adjoint: pressure must be positive");
+  if (m->host.K > 128) return set_err(CHEM_ESIZE, "chem_adjoint: more than 128 species");
+  if (ncells == 0) return CHEM_OK;
+  if (!rec || !nsteps || !status || !gT || !gY || !gT0 || !gY0)
+    return set_err(CHEM_EINVAL, "chem_adjoint: NULL argument");
+  const void* arrays[9] = {rec, nsteps, status, gT, gY, gT0, gY0, g_lnA, g_lnA_cells};
+  for (const void* ptr : arrays)
+    if (ptr && !is_device_ptr(ptr)) return set_err(CHEM_EINVAL, "chem_adjoint: device arrays only");
+  const size_t need = adjoint_workspace_doubles(m->host.R, ncells, g_lnA_cells != nullptr);
+  if (need > m->cap_adj_ws) {
+    cudaFree(m->d_adj_ws);
+    m->d_adj_ws = nullptr;
+    m->cap_adj_ws = 0;
+    CK(cudaMalloc(&m->d_adj_ws, need * sizeof(double)));
+    m->cap_adj_ws = need;
+  }
+  if (!m->d_adj_counters) CK(cudaMalloc(&m->d_adj_counters, 2 * sizeof(int)));
+  std::string err;
+  const int rc = adjoint_enqueue(m->dev, m->num_sms, m->max_smem, p_Pa * 10.0, ncells, rec, max_steps_rec, nsteps,
+                                 status, gT, gY, gT0, gY0, g_lnA, g_lnA_cells, m->d_adj_ws, m->d_adj_counters,
+                                 static_cast<cudaStream_t>(stream), err);
+  if (rc) return set_err(rc, err);
+  return CHEM_OK;
+}
+
+int chem_get_lnA(const chem_mech* m, double* lnA) {
+  if (!m || !lnA) return set_err(CHEM_EINVAL, "chem_get_lnA: NULL argument");
+  const HostMech& h = m->host;
+  for (int dr = 0; dr < h.R; ++dr) lnA[h.order[dr]] = h.rxd[(size_t)dr * kRxDoubles];
+  return CHEM_OK;
+}
+
+int chem_set_lnA(chem_mech* m, const double* lnA) {
+  if (!m || !lnA) return set_err(CHEM_EINVAL, "chem_set_lnA: NULL argument");
+  HostMech& h = m->host;
+  for (int r = 0; r < h.R; ++r)
+    if (!std::isfinite(lnA[r])) return set_err(CHEM_EINVAL, "chem_set_lnA: non-finite value");
+  for (int dr = 0; dr < h.R; ++dr) h.rxd[(size_t)dr * kRxDoubles] = lnA[h.order[dr]];
+  // the device tables are read by kernels in flight on any stream: wait for them first
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(const_cast<double*>(m->dev.rxd), h.rxd.data(), h.rxd.size() * sizeof(double),
+                cudaMemcpyHostToDevice));
   return CHEM_OK;
 }
 
@@ -1673,6 +1048,7 @@ int chem_integrate_noalloc(const chem_mech* mc, double p_Pa, double* T, double* 
   int32_t* d_steps = reinterpret_cast<int32_t*>(s + kNoAllocCounters);
   int32_t* d_rej = d_steps + kNoAllocMaxCells;
   IntegrateArgs a;
+  std::memset(&a, 0, sizeof(a));
   a.p = p_Pa * 10.0; a.dt = dt; a.rtol = rtol; a.atol = atol;
   a.T = T; a.Y = Y; a.h_inout = h_inout; a.status = status;
   a.steps_out = d_steps; a.rej_out = d_rej;

@@ -16,7 +16,8 @@ def _declared():
 
 def test_header_declares_the_boundary():
     names = _declared()
-    for required in ("chem_load_mechanism", "chem_rates", "chem_jacobian", "chem_integrate", "chem_last_error"):
+    for required in ("chem_load_mechanism", "chem_rates", "chem_jacobian", "chem_integrate", "chem_integrate_record",
+                     "chem_adjoint", "chem_last_error"):
         assert required in names
 
 
