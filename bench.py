@@ -13,6 +13,11 @@ on a bounded sample of the same field on the host cores.
 
 `--impl reference` times the CPU oracle itself (the reference implementation of this repo's
 method) on a bounded sample per step.
+
+`--workload adjoint` times the differentiated solve instead: 16 384 cells of the igniting band
+(53 species, T ~ U[1000, 1300] K, 20 atm, dt = 1e-4 s); one step = chem_integrate_record +
+chem_adjoint for a random dL/dphi(dt), reporting the forward and backward times, their ratio
+and the checkpoint memory.
 """
 from __future__ import annotations
 
@@ -53,7 +58,7 @@ def parse_args():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--cells", type=int, default=0, help="cells per rank (0 = the full 65536-cell field)")
     ap.add_argument("--dt", type=float, default=0.0, help="override the CFD time step (profiling small cases)")
-    ap.add_argument("--workload", choices=["shear", "uneven"], default="shear",
+    ap.add_argument("--workload", choices=["shear", "uneven", "adjoint"], default="shear",
                     help="shear: 53-species shear layer (the headline); uneven: 100-species igniting/cold/burnt field")
     ap.add_argument("--order", choices=["shuffled", "blocked"], default="blocked", help="cell order of --workload uneven")
     ap.add_argument("--batch-cells", type=int, default=0,
@@ -183,10 +188,129 @@ def algorithmic_flops(steps: np.ndarray, rejects: np.ndarray):
     return attempt * total_attempts + accepted * total_steps, {"per_attempt": attempt, "per_accepted": accepted}
 
 
+def run_adjoint(args, world, rank, local):
+    """Forward with checkpoints + discrete adjoint on the igniting band (see the module doc)."""
+    import torch
+    from paper_2105_12070_gb300 import chem, synth
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n = args.cells or 16384
+    w = synth.workload_igniting(n)
+    if args.dt > 0:
+        w["dt"] = args.dt
+    mech = chem.Mechanism(w["mech"].write_temp())
+    N, K, R = mech.N, mech.K, mech.R
+    rng = np.random.default_rng(7)
+    T_host = torch.from_numpy(w["T"].copy()).pin_memory()
+    Y_host = torch.from_numpy(w["Y"].copy()).pin_memory()
+    gT_host = torch.from_numpy(rng.normal(size=n) * 1e-3).pin_memory()
+    gY_host = torch.from_numpy(rng.normal(size=(K, n))).pin_memory()
+    outs = [torch.empty(n, dtype=torch.float64).pin_memory(), torch.empty((K, n), dtype=torch.float64).pin_memory(),
+            torch.empty(R, dtype=torch.float64).pin_memory()]
+    T = torch.empty_like(T_host, device="cuda")
+    Y = torch.empty_like(Y_host, device="cuda")
+    gT, gY = torch.empty_like(gT_host, device="cuda"), torch.empty_like(gY_host, device="cuda")
+    gT0, gY0 = torch.empty_like(gT), torch.empty_like(gY)
+    g_lnA = torch.empty(R, dtype=torch.float64, device="cuda")
+    status = torch.zeros(n, dtype=torch.int32, device="cuda")
+    nsteps = torch.zeros(n, dtype=torch.int32, device="cuda")
+    # checkpoint capacity: the accepted-step count of a plain FP64 pass, plus a margin
+    T.copy_(T_host)
+    Y.copy_(Y_host)
+    chem.chem_integrate(mech, w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], status=status)
+    steps = torch.zeros(n, dtype=torch.int32, device="cuda")
+    chem.chem_last_cell_counters(mech, steps, None)
+    cap = int(steps.max().item()) + 16
+    rec = torch.empty((n, cap, N + 1), dtype=torch.float64, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one_step(m):
+        flush.fill_(1.0)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        e[0].record(stream)
+        T[:m].copy_(T_host[:m], non_blocking=True)
+        Y[:, :m].copy_(Y_host[:, :m], non_blocking=True)
+        gT[:m].copy_(gT_host[:m], non_blocking=True)
+        gY[:, :m].copy_(gY_host[:, :m], non_blocking=True)
+        e[1].record(stream)
+        Ts, Ys = (T, Y) if m == n else (T[:m].contiguous(), Y[:, :m].contiguous())
+        chem.chem_integrate_record(mech, w["p_Pa"], Ts, Ys, w["dt"], rec[:m], nsteps[:m], status[:m],
+                                   rtol=w["rtol"], atol=w["atol"])
+        e[2].record(stream)
+        gTs, gYs = (gT, gY) if m == n else (gT[:m].contiguous(), gY[:, :m].contiguous())
+        gT0s, gY0s = (gT0, gY0) if m == n else (gT0[:m].contiguous(), gY0[:, :m].contiguous())
+        chem.chem_adjoint(mech, w["p_Pa"], rec[:m], nsteps[:m], status[:m], gTs, gYs, gT0s, gY0s, g_lnA=g_lnA)
+        e[3].record(stream)
+        outs[0][:m].copy_(gT0s, non_blocking=True)
+        outs[1][:, :m].copy_(gY0s, non_blocking=True)
+        outs[2].copy_(g_lnA, non_blocking=True)
+        e[4].record(stream)
+        e[4].synchronize()
+        return e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3]), e[0].elapsed_time(e[4])
+
+    warm = min(n, 152)
+    for _ in range(args.warmup):
+        one_step(warm)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    fwd = bwd = tot = 0.0
+    for _ in range(args.steps):
+        a, b, c = one_step(n)
+        fwd += a
+        bwd += b
+        tot += c
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([fwd, bwd, tot], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        fwd, bwd, tot = t.tolist()
+    ns = nsteps.cpu().numpy()
+    st = status.cpu().numpy()
+    cells = n * world * args.steps
+    line = {
+        "metric": "cells/s, forward with checkpoints + discrete adjoint (53 sp, igniting band, dt 1e-4 s)",
+        "value": cells / ((fwd + bwd) / 1e3), "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": (fwd + bwd) / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "cells": n, "species": K, "reactions": R, "dt_s": w["dt"],
+                   "p_atm": w["p_Pa"] / 101325.0, "rtol": w["rtol"], "atol": w["atol"],
+                   "warmup_cells": warm, "l2": "flushed between steps (256 MiB write)",
+                   "gradient": "dL/d(T0, Y0) per cell and dL/dlnA summed over cells, L random linear"},
+        "forward_ms": fwd / args.steps, "backward_ms": bwd / args.steps, "backward_over_forward": bwd / fwd,
+        "checkpoint": {"bytes_allocated": int(n * cap * (N + 1) * 8), "bytes_used": int(ns.sum()) * (N + 1) * 8,
+                       "steps_per_cell_max": int(ns.max()), "steps_per_cell_mean": float(ns.mean()),
+                       "peak_device_bytes": int(torch.cuda.max_memory_allocated())},
+        "e2e": {"value": cells / (tot / 1e3), "unit": "cells/s",
+                "h2d_bytes_per_step": int((T_host.numel() + Y_host.numel() + gT_host.numel() + gY_host.numel()) * 8),
+                "d2h_bytes_per_step": int((n + K * n + R) * 8)},
+        "gpu_launches": 4 * args.steps,
+        "roofline": None,
+        "clocks": clk,
+        "cells_status": {str(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
     from paper_2105_12070_gb300 import synth
+    if args.workload == "adjoint" and args.impl == "gpu":
+        return run_adjoint(args, world, rank, local)
     if args.workload == "uneven":
         w = synth.workload_uneven(args.cells or 262144, args.order)
     else:

@@ -74,3 +74,21 @@ def test_closed_form_chain_sensitivities():
     assert abs(d2[1]) <= tol and abs(d2[2] - dB_l2) <= tol
     # the chain is linear in the initial amount of A
     assert abs(da[1] - e1) <= tol and abs(da[2] - k1 / (k2 - k1) * (e1 - e2)) <= tol
+
+
+def test_jacobian_directional_derivative():
+    """jacobian_dir: df = J d, and dJ equals central differences of the analytical Jacobian."""
+    mech, p, phi, _ = _small_cell(11)
+    rng = np.random.default_rng(7)
+    d = rng.normal(size=mech.N) * np.maximum(np.abs(phi), 1e-6)
+    f, J, df, dJ = mech.jacobian_dir(p, phi, dphi=d)
+    T, Y = phi[:1], np.concatenate([phi[1:], [1.0 - phi[1:].sum()]])[:, None]
+    np.testing.assert_array_equal(J, mech.jacobian(p, T, Y)[0])
+    np.testing.assert_allclose(df, J @ d, rtol=1e-10, atol=1e-10 * np.abs(J @ d).max())
+    eps = 1e-5
+
+    def jac(x):
+        return mech.jacobian(p, x[:1], np.concatenate([x[1:], [1.0 - x[1:].sum()]])[:, None])[0]
+
+    fd = (jac(phi + eps * d) - jac(phi - eps * d)) / (2 * eps)
+    assert np.max(np.abs(fd - dJ)) <= 1e-6 * np.max(np.abs(dJ))
