@@ -191,7 +191,7 @@ def algorithmic_flops(steps: np.ndarray, rejects: np.ndarray):
 def run_adjoint(args, world, rank, local):
     """Forward with checkpoints + discrete adjoint on the igniting band (see the module doc)."""
     import torch
-    from paper_2105_12070_gb300 import chem, synth
+    from paper_2105_12070_gb300 import chem, ranks, synth
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -244,6 +244,7 @@ def run_adjoint(args, world, rank, local):
         gTs, gYs = (gT, gY) if m == n else (gT[:m].contiguous(), gY[:, :m].contiguous())
         gT0s, gY0s = (gT0, gY0) if m == n else (gT0[:m].contiguous(), gY0[:, :m].contiguous())
         chem.chem_adjoint(mech, w["p_Pa"], rec[:m], nsteps[:m], status[:m], gTs, gYs, gT0s, gY0s, g_lnA=g_lnA)
+        ranks.sum_lnA_grad(g_lnA)  # the one exchange step (N > 1): sum of the per-rank gradients
         e[3].record(stream)
         outs[0][:m].copy_(gT0s, non_blocking=True)
         outs[1][:, :m].copy_(gY0s, non_blocking=True)
@@ -269,11 +270,7 @@ def run_adjoint(args, world, rank, local):
         tot += c
     torch.cuda.synchronize()
     clk = clocks.stop()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([fwd, bwd, tot], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        fwd, bwd, tot = t.tolist()
+    fwd, bwd, tot = ranks.max_over_ranks([fwd, bwd, tot], device="cuda")
     ns = nsteps.cpu().numpy()
     st = status.cpu().numpy()
     cells = n * world * args.steps
@@ -321,7 +318,7 @@ def main():
         return run_reference(args, w, world, rank)
 
     import torch
-    from paper_2105_12070_gb300 import chem
+    from paper_2105_12070_gb300 import chem, ranks
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -377,11 +374,7 @@ def main():
         e2e_ms += e
     torch.cuda.synchronize()
     clk = clocks.stop()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([kern_ms, e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        kern_ms, e2e_ms = t.tolist()
+    kern_ms, e2e_ms = ranks.max_over_ranks([kern_ms, e2e_ms], device="cuda")
     st_np = status.cpu().numpy()
     steps = torch.zeros(n_total, dtype=torch.int32, device="cuda")
     rej = torch.zeros_like(steps)
