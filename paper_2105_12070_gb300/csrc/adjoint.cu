@@ -15,9 +15,11 @@
 // in dual numbers along u; its value part is J(y), which gives the stage-1 term J(y)^T v_1.
 //
 // Per accepted step and cell: one FP64 Jacobian at y_n and the LU of W (as in the solve), the
-// four stages (two rate evaluations, four solves), four transposed solves, FP64 Jacobians at Y_3
-// and Y_2, and four Jacobian evaluations in dual numbers.  One cell per CTA of 8 warps (the
-// working set, ~130 KB for 53 species, fills most of the shared memory), cells from a queue.
+// four stages (two rate evaluations, four solves), four transposed solves, products J^T v at
+// Y_3 and Y_2, and four evaluations of J^T v_i in dual numbers along u_i.  The J^T products are
+// matrix-free (cell_jacobian_vjp): weighted column sums of d omega/dC built from the
+// per-reaction data, so only the Jacobian at y_n (for W) is ever formed.  That keeps the working
+// set near 95 KB for 53 species: two cells of 4 warps per CTA, cells from a queue.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,32 +31,36 @@
 
 namespace {
 
-constexpr int kAdjG = 8;  // warps per cell
-
 // Per-cell shared-memory plan of the adjoint (in doubles).
 struct AdjPlan {
-  int N, n2, SA, nR2, nM2;
-  int off_M, off_vec, off_ev, off_yd, off_P, off_gA, off_piv, off_red, total;
+  int N, n2, SA, nR2, nM2, nP2, nAB2, G;
+  int off_M, off_vec, off_ev, off_ab, off_tz, off_yd, off_P, off_gA, off_piv, off_red, total;
 };
 
-AdjPlan make_adj_plan(int K, int R, int n_pd, int G) {
+AdjPlan make_adj_plan(int K, int R, int n_pd, int n_pairs, int G) {
   AdjPlan p;
+  p.G = G;
   p.N = K;
   p.n2 = round2(K);
   p.SA = round2(std::max(K * K, 8 * R));
   p.nR2 = round2(R);
   p.nM2 = round2(std::max(n_pd, 1));
-  // four matrix buffers: M0 = LU of W, M1 = Jacobian (and its per-reaction scratch), M2 = the
-  // Jacobian's Z scratch; in the dual-number passes M0..M1 hold the dual Jacobian and M2..M3 its
-  // dual Z
+  p.nP2 = round2(std::max(n_pairs, 1));
+  p.nAB2 = round2(2 * R + 2 * n_pd);
+  // matrix region, reused by the phases of a step: the Jacobian at y_n (scratch, then -J, then
+  // W and its LU in place) with its Z scratch behind it; the LU with the per-reaction scratch of
+  // the stage-state evaluations behind it; the dual-number per-reaction scratch
   p.off_M = 0;
-  // 20 vectors: y f ys rhs u0..u3 ub0..ub3 v0..v3 ybar lam invdiag wv
-  p.off_vec = 4 * p.SA;
-  // evaluation arrays, sized as duals: 12 species arrays, q, M, pair coefficients (8 n2)
-  p.off_ev = p.off_vec + 20 * p.n2;
-  p.off_yd = p.off_ev + 2 * (20 * p.n2 + p.nR2 + p.nM2);
-  p.off_P = p.off_yd + 4 * p.n2;  // dual state and dual source term
-  p.off_gA = p.off_P + 2 * p.nR2;  // P_r (dual), then the cell's ln A gradient
+  const int msize = round2(std::max({p.SA + K * K, K * K + 8 * R, 16 * R}));
+  // 18 vectors: y f ys rhs u0..u3 ub0..ub3 (v_i overwrite ub_i) ybar lam invdiag wv (+2 spare)
+  p.off_vec = msize;
+  // evaluation arrays, sized as duals: 12 species arrays, q, [M], pair coefficients
+  p.off_ev = p.off_vec + 18 * p.n2;
+  p.off_ab = p.off_ev + 2 * (12 * p.n2 + p.nR2 + p.nM2 + p.nP2);
+  p.off_tz = p.off_ab + 2 * p.nAB2;     // per-reaction weights of the J^T product (duals)
+  p.off_yd = p.off_tz + 2 * 2 * p.n2;   // weighted column sums (duals)
+  p.off_P = p.off_yd + 6 * p.n2;        // dual state, dual source term, dual J^T v
+  p.off_gA = p.off_P + 2 * p.nR2;       // P_r (dual), then the cell's ln A gradient
   p.off_piv = p.off_gA + p.nR2;
   p.off_red = p.off_piv + round2(K + 2);
   p.total = round2(p.off_red + 6 * G + 2);
@@ -62,35 +68,36 @@ AdjPlan make_adj_plan(int K, int R, int n_pd, int G) {
 }
 
 struct AdjMem {
-  double *M0, *M1, *M2;
-  double *y, *f, *ys, *rhs, *u[4], *ub[4], *v[4], *ybar, *lam, *invdiag, *wv;
-  Dual *yd, *fd;
+  double* M;
+  double *y, *f, *ys, *rhs, *u[4], *v[4], *ybar, *lam, *invdiag, *wv;
+  Dual *yd, *fd, *od;
   double* gA;
   int *piv, *perm, *slot;
   double* red;
+  int n2;  // vector stride: u[k] = u[0] + k n2, v[k] = v[0] + k n2 (loops index them arithmetically,
+           // so the pointer arrays stay in registers)
 };
 
 __device__ inline AdjMem carve_adj(double* base, const AdjPlan& p) {
   AdjMem w;
-  w.M0 = base + p.off_M;
-  w.M1 = w.M0 + p.SA;
-  w.M2 = w.M1 + p.SA;
+  w.M = base + p.off_M;
   double* v = base + p.off_vec;
   const int n = p.n2;
   w.y = v; w.f = v + n; w.ys = v + 2 * n; w.rhs = v + 3 * n;
   for (int i = 0; i < 4; ++i) {
     w.u[i] = v + (4 + i) * n;
-    w.ub[i] = v + (8 + i) * n;
-    w.v[i] = v + (12 + i) * n;
+    w.v[i] = v + (8 + i) * n;  // holds ub_i until the transposed solve turns it into v_i
   }
-  w.ybar = v + 16 * n; w.lam = v + 17 * n; w.invdiag = v + 18 * n; w.wv = v + 19 * n;
+  w.ybar = v + 12 * n; w.lam = v + 13 * n; w.invdiag = v + 14 * n; w.wv = v + 15 * n;
   w.yd = reinterpret_cast<Dual*>(base + p.off_yd);
   w.fd = w.yd + n;
+  w.od = w.fd + n;
   w.gA = base + p.off_gA;
   w.piv = reinterpret_cast<int*>(base + p.off_piv);
   w.perm = w.piv + p.N + 2;
   w.red = base + p.off_red;
-  w.slot = reinterpret_cast<int*>(base + p.off_red + 6 * kAdjG);
+  w.slot = reinterpret_cast<int*>(base + p.off_red + 6 * p.G);
+  w.n2 = n;
   return w;
 }
 
@@ -109,81 +116,67 @@ __device__ inline EvalMem<S> adj_eval_mem(double* base, const AdjPlan& p) {
   return m;
 }
 
-// out = J^T v for the stored -J (NJ): out[c] = -sum_a NJ[a][c] v[a], one thread per column.
 template <int G>
-__device__ inline void jt_times(const Grp<G>& g, const double* NJ, int N, const double* v, double* out) {
-  for (int c = g.t; c < N; c += Grp<G>::NT) {
-    double s0 = 0.0, s1 = 0.0;
-    int a = 0;
-    for (; a + 1 < N; a += 2) {
-      s0 = fma(NJ[a * N + c], v[a], s0);
-      s1 = fma(NJ[(a + 1) * N + c], v[a + 1], s1);
-    }
-    if (a < N) s0 = fma(NJ[a * N + c], v[a], s0);
-    out[c] = -(s0 + s1);
-  }
-}
-
-template <int G>
-__device__ inline void solve_t(const Grp<G>& g, const AdjMem& w, int N, const double* b, double* x) {
-  if (g.warp() == 0) warp_lu_solve_t(w.M0, N, w.perm, w.invdiag, b, x);
+__device__ inline void solve_t(const Grp<G>& g, const AdjMem& w, int N, double* x) {
+  if (g.warp() == 0) warp_lu_solve_t(w.M, N, w.perm, w.invdiag, x, x);
   g.sync();
 }
 
 // One accepted step backwards: w.y = y_n, h = h_n, w.lam = dL/dy_{n+1} on entry; dL/dy_n in
 // w.lam and the step's ln A terms added to w.gA on exit.  False if W is exactly singular.
 template <int G>
-__device__ bool adjoint_step(const DevMech& m, const Grp<G>& g, double p, double h, const AdjMem& w,
-                             const EvalMem<double>& ed, const EvalMem<Dual>& eD, double* Pd, Dual* PD) {
+__device__ bool adjoint_step(const DevMech& m, const Grp<G>& g, const AdjPlan& plan, double p, double h,
+                             const AdjMem& w, const EvalMem<double>& ed, const EvalMem<Dual>& eD, double* abd,
+                             Dual* abD, double* tzd, Dual* tzD, double* Pd, Dual* PD) {
   constexpr int NT = Grp<G>::NT;
   const int N = m.N, R = m.R;
   const double gh = 1.0 / (c_gamma * h);
   const double invh = 1.0 / h;
+  double* LU = w.M;            // -J(y_n), then W, then its factors
+  double* scr = w.M + N * N;   // per-reaction scratch of the stage-state evaluations
   // J(y) and the factors of W (as in the solve)
-  const CellScalars s0 = cell_rates(m, g, p, w.y, w.f, ed, w.M1, true);
-  cell_jacobian(m, g, s0, w.f, ed, w.M1, w.M2);
-  for (int e = g.t; e < N * N; e += NT) w.M0[e] = w.M1[e];
+  const CellScalars s0 = cell_rates(m, g, p, w.y, w.f, ed, LU, true);
+  cell_jacobian(m, g, s0, w.f, ed, LU, w.M + plan.SA);
+  for (int i = g.t; i < N; i += NT) LU[i * N + i] += gh;
   g.sync();
-  for (int i = g.t; i < N; i += NT) w.M0[i * N + i] += gh;
-  g.sync();
-  if (!cell_lu<G, double>(g, w.M0, N, w.piv, w.perm, w.invdiag)) return false;
+  if (!cell_lu<G, double>(g, LU, N, w.piv, w.perm, w.invdiag)) return false;
   // the four stage increments
   for (int i = g.t; i < N; i += NT) w.u[0][i] = w.f[i];
   g.sync();
-  cell_solve(g, w.M0, N, w.perm, w.invdiag, w.u[0]);
+  cell_solve(g, LU, N, w.perm, w.invdiag, w.u[0]);
   for (int i = g.t; i < N; i += NT) w.ys[i] = fma(c_a21, w.u[0][i], w.y[i]);
   g.sync();
   cell_rates(m, g, p, w.ys, w.f, ed, (double*)nullptr, false);
   for (int i = g.t; i < N; i += NT) w.u[1][i] = fma(c_c21 * invh, w.u[0][i], w.f[i]);
   g.sync();
-  cell_solve(g, w.M0, N, w.perm, w.invdiag, w.u[1]);
+  cell_solve(g, LU, N, w.perm, w.invdiag, w.u[1]);
   for (int i = g.t; i < N; i += NT) w.ys[i] = w.y[i] + c_a31 * w.u[0][i] + c_a32 * w.u[1][i];
   g.sync();
   cell_rates(m, g, p, w.ys, w.f, ed, (double*)nullptr, false);
   for (int i = g.t; i < N; i += NT) w.u[2][i] = w.f[i] + invh * (c_c31 * w.u[0][i] + c_c32 * w.u[1][i]);
   g.sync();
-  cell_solve(g, w.M0, N, w.perm, w.invdiag, w.u[2]);
+  cell_solve(g, LU, N, w.perm, w.invdiag, w.u[2]);
   for (int i = g.t; i < N; i += NT)
     w.u[3][i] = w.f[i] + invh * (c_c41 * w.u[0][i] + c_c42 * w.u[1][i] + c_c43 * w.u[2][i]);
   g.sync();
-  cell_solve(g, w.M0, N, w.perm, w.invdiag, w.u[3]);
-  // reverse sweep over the stages
+  cell_solve(g, LU, N, w.perm, w.invdiag, w.u[3]);
+  // reverse sweep over the stages (w.v[i] holds ub_i, then v_i = W^-T ub_i)
   for (int i = g.t; i < N; i += NT) {
     const double l = w.lam[i];
     w.ybar[i] = l;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) w.ub[k][i] = c_m[k] * l;
+    for (int k = 0; k < 4; ++k) w.v[k][i] = c_m[k] * l;
   }
   g.sync();
-  solve_t(g, w, N, w.ub[3], w.v[3]);
+  solve_t(g, w, N, w.v[3]);
   for (int i = g.t; i < N; i += NT) {
     const double x = invh * w.v[3][i];
-    w.ub[2][i] = fma(c_c43, x, w.ub[2][i]);
-    w.ub[1][i] = fma(c_c42, x, w.ub[1][i]);
-    w.ub[0][i] = fma(c_c41, x, w.ub[0][i]);
+    w.v[2][i] = fma(c_c43, x, w.v[2][i]);
+    w.v[1][i] = fma(c_c42, x, w.v[1][i]);
+    w.v[0][i] = fma(c_c41, x, w.v[0][i]);
   }
   g.sync();
-  solve_t(g, w, N, w.ub[2], w.v[2]);
+  solve_t(g, w, N, w.v[2]);
   // stages 3 and 4 share f(Y_3): J(Y_3)^T (v_3 + v_4) and the ln A terms with that weight
   for (int i = g.t; i < N; i += NT) {
     w.wv[i] = w.v[2][i] + w.v[3][i];
@@ -191,58 +184,44 @@ __device__ bool adjoint_step(const DevMech& m, const Grp<G>& g, double p, double
   }
   g.sync();
   {
-    const CellScalars s3 = cell_rates<G, double, true>(m, g, p, w.ys, w.f, ed, w.M1, true, w.wv, Pd);
-    cell_jacobian(m, g, s3, w.f, ed, w.M1, w.M2);
+    const CellScalars s3 = cell_rates<G, double, true>(m, g, p, w.ys, w.f, ed, scr, true, w.wv, Pd);
+    cell_jacobian_vjp(m, g, s3, w.f, ed, scr, w.wv, abd, tzd, w.rhs);
   }
-  jt_times(g, w.M1, N, w.wv, w.rhs);
   for (int r = g.t; r < R; r += NT) w.gA[r] += Pd[r];
-  g.sync();
   for (int i = g.t; i < N; i += NT) {
     const double x = invh * w.v[2][i], r = w.rhs[i];
-    w.ub[1][i] += c_c32 * x + c_a32 * r;
-    w.ub[0][i] += c_c31 * x + c_a31 * r;
+    w.v[1][i] += c_c32 * x + c_a32 * r;
+    w.v[0][i] += c_c31 * x + c_a31 * r;
     w.ybar[i] += r;
   }
   g.sync();
-  solve_t(g, w, N, w.ub[1], w.v[1]);
+  solve_t(g, w, N, w.v[1]);
   for (int i = g.t; i < N; i += NT) w.ys[i] = fma(c_a21, w.u[0][i], w.y[i]);
   g.sync();
   {
-    const CellScalars s2 = cell_rates<G, double, true>(m, g, p, w.ys, w.f, ed, w.M1, true, w.v[1], Pd);
-    cell_jacobian(m, g, s2, w.f, ed, w.M1, w.M2);
+    const CellScalars s2 = cell_rates<G, double, true>(m, g, p, w.ys, w.f, ed, scr, true, w.v[1], Pd);
+    cell_jacobian_vjp(m, g, s2, w.f, ed, scr, w.v[1], abd, tzd, w.rhs);
   }
-  jt_times(g, w.M1, N, w.v[1], w.rhs);
   for (int r = g.t; r < R; r += NT) w.gA[r] += Pd[r];
-  g.sync();
   for (int i = g.t; i < N; i += NT) {
     const double r = w.rhs[i];
-    w.ub[0][i] += c_c21 * invh * w.v[1][i] + c_a21 * r;
+    w.v[0][i] += c_c21 * invh * w.v[1][i] + c_a21 * r;
     w.ybar[i] += r;
   }
   g.sync();
-  solve_t(g, w, N, w.ub[0], w.v[0]);
-  // derivatives of J and of v . df/dlnA along each u_i at y (dual numbers); the value part of
-  // the first pass is J(y) itself and gives the stage-1 terms
-  Dual* JD = reinterpret_cast<Dual*>(w.M0);
-  Dual* ZD = reinterpret_cast<Dual*>(w.M2);
+  solve_t(g, w, N, w.v[0]);
+  // derivatives of J^T v_i and of v_i . df/dlnA along u_i at y (dual numbers): the derivative
+  // parts are the terms of W's dependence on y; the value part of the first pass is
+  // J(y)^T v_1 and v_1 . df/dlnA(y), the stage-1 terms
+  Dual* scrD = reinterpret_cast<Dual*>(w.M);
   for (int k = 0; k < 4; ++k) {
-    for (int i = g.t; i < N; i += NT) w.yd[i] = Dual(w.y[i], w.u[k][i]);
+    const double* uk = w.u[0] + k * w.n2;
+    const double* vk = w.v[0] + k * w.n2;
+    for (int i = g.t; i < N; i += NT) w.yd[i] = Dual(w.y[i], uk[i]);
     g.sync();
-    const CellScalarsT<Dual> sd = cell_rates<G, Dual, true>(m, g, p, w.yd, w.fd, eD, JD, true, w.v[k], PD);
-    cell_jacobian(m, g, sd, w.fd, eD, JD, ZD);
-    const double* vk = w.v[k];
-    for (int c = g.t; c < N; c += NT) {
-      double s = 0.0;
-      if (k == 0) {
-        for (int a = 0; a < N; ++a) {
-          const Dual x = JD[a * N + c];
-          s = fma(x.v + x.d, vk[a], s);
-        }
-      } else {
-        for (int a = 0; a < N; ++a) s = fma(JD[a * N + c].d, vk[a], s);
-      }
-      w.ybar[c] -= s;
-    }
+    const CellScalarsT<Dual> sd = cell_rates<G, Dual, true>(m, g, p, w.yd, w.fd, eD, scrD, true, vk, PD);
+    cell_jacobian_vjp(m, g, sd, w.fd, eD, scrD, vk, abD, tzD, w.od);
+    for (int i = g.t; i < N; i += NT) w.ybar[i] += (k == 0) ? w.od[i].v + w.od[i].d : w.od[i].d;
     for (int r = g.t; r < R; r += NT) w.gA[r] += (k == 0) ? PD[r].v + PD[r].d : PD[r].d;
     g.sync();
   }
@@ -266,7 +245,7 @@ struct AdjArgs {
 };
 
 template <int G>
-__global__ void __launch_bounds__(32 * G, 1) adjoint_kernel(DevMech m, AdjPlan plan, AdjArgs a) {
+__global__ void __launch_bounds__(256, 1) adjoint_kernel(DevMech m, AdjPlan plan, AdjArgs a) {
   extern __shared__ __align__(16) double smem[];
   constexpr int NT = Grp<G>::NT;
   Grp<G> g;
@@ -280,6 +259,10 @@ __global__ void __launch_bounds__(32 * G, 1) adjoint_kernel(DevMech m, AdjPlan p
   const EvalMem<Dual> eD = adj_eval_mem<Dual>(base, plan);
   double* Pd = base + plan.off_P;
   Dual* PD = reinterpret_cast<Dual*>(base + plan.off_P);
+  double* abd = base + plan.off_ab;
+  Dual* abD = reinterpret_cast<Dual*>(abd);
+  double* tzd = base + plan.off_tz;
+  Dual* tzD = reinterpret_cast<Dual*>(tzd);
   const int N = m.N, K = m.K, R = m.R;
   const int64_t nc = a.ncells;
   for (;;) {
@@ -300,7 +283,7 @@ __global__ void __launch_bounds__(32 * G, 1) adjoint_kernel(DevMech m, AdjPlan p
       for (int i = g.t; i < N; i += NT) w.y[i] = ck[i];
       const double h = ck[N];
       g.sync();
-      if (!adjoint_step(m, g, a.p, h, w, ed, eD, Pd, PD)) {
+      if (!adjoint_step(m, g, plan, a.p, h, w, ed, eD, abd, abD, tzd, tzD, Pd, PD)) {
         ok = false;
         if (g.t == 0) atomicAdd(a.nfail, 1);
         break;
@@ -352,14 +335,18 @@ int adjoint_enqueue(const DevMech& d, int num_sms, size_t max_smem, double p_cgs
                     int rec_cap, const int32_t* nsteps, const int32_t* status, const double* gT, const double* gY,
                     double* gT0, double* gY0, double* g_lnA, double* g_lnA_cells, double* ws, int* counters,
                     cudaStream_t st, std::string& err) {
-  const AdjPlan plan = make_adj_plan(d.K, d.R, d.n_pd, kAdjG);
-  const size_t smem = (size_t)plan.total * sizeof(double);
+  // launch shape: 8 warps per CTA; two cells of 4 warps when both working sets fit, else one
+  // cell of 8 warps
+  int G = 4, cpc = 2;
+  AdjPlan plan = make_adj_plan(d.K, d.R, d.n_pd, d.n_pairs, G);
+  if ((size_t)plan.total * sizeof(double) * cpc > max_smem) {
+    G = 8;
+    cpc = 1;
+    plan = make_adj_plan(d.K, d.R, d.n_pd, d.n_pairs, G);
+  }
+  const size_t smem = (size_t)plan.total * sizeof(double) * cpc;
   if (smem > max_smem) {
     err = "chem_adjoint: working set of one cell (" + std::to_string(smem) + " B) exceeds a CTA's shared memory";
-    return CHEM_ESIZE;
-  }
-  if (d.n_pairs > 8 * plan.n2) {
-    err = "chem_adjoint: too many pressure-dependent (row, reaction) pairs";
     return CHEM_ESIZE;
   }
   auto fail = [&](cudaError_t e, const char* what) {
@@ -368,11 +355,12 @@ int adjoint_enqueue(const DevMech& d, int num_sms, size_t max_smem, double p_cgs
   };
   cudaError_t e = cudaMemsetAsync(counters, 0, 2 * sizeof(int), st);
   if (e != cudaSuccess) return fail(e, "cudaMemsetAsync");
-  const void* fn = (const void*)adjoint_kernel<kAdjG>;
+  const void* fn = G == 4 ? (const void*)adjoint_kernel<4> : (const void*)adjoint_kernel<8>;
+  const int threads = 32 * G * cpc;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return fail(e, "cudaFuncSetAttribute");
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 32 * kAdjG, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem);
   if (e != cudaSuccess) return fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (occ < 1) {
     err = "chem_adjoint: kernel cannot be resident with its shared memory";
@@ -384,8 +372,10 @@ int adjoint_enqueue(const DevMech& d, int num_sms, size_t max_smem, double p_cgs
   a.p = p_cgs; a.rec = rec; a.rec_cap = rec_cap; a.nsteps = nsteps; a.status = status;
   a.gT = gT; a.gY = gY; a.gT0 = gT0; a.gY0 = gY0; a.gcell = gcell; a.ncells = ncells;
   a.queue = counters; a.nfail = counters + 1;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ncells, (int64_t)num_sms * occ));
-  adjoint_kernel<kAdjG><<<grid, 32 * kAdjG, smem, st>>>(d, plan, a);
+  const int64_t ctas = (ncells + cpc - 1) / cpc;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, (int64_t)num_sms * occ));
+  if (G == 4) adjoint_kernel<4><<<grid, threads, smem, st>>>(d, plan, a);
+  else adjoint_kernel<8><<<grid, threads, smem, st>>>(d, plan, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(e, "adjoint kernel launch");
   if (g_lnA) {

@@ -419,9 +419,10 @@ __device__ inline void troe(const double* fo, S T, S invT, S Pr, S& F, S& dlF, S
 }
 
 // Evaluates f(y) into f[0..N).  With jac, also leaves per-reaction derivative data in
-// scr[r*8 + 0..7] = {dq/dC at the 4 distinct slot species, phi (coefficient of the
-// efficiencies), sum_j dq/dC_j C_j, dq/dT at fixed C, reaction enthalpy (erg/mol)} and the
-// species production rates in w.omega.
+// scr[u * R + r], u = 0..7: {dq/dC at the 4 distinct slot species, phi (coefficient of the
+// efficiencies), sum_j dq/dC_j C_j, dq/dT at fixed C, reaction enthalpy (erg/mol)} (rows of R,
+// so that the threads of consecutive reactions store to consecutive words), and the species
+// production rates in w.omega.
 // With kP (adjoint use, requires jac) it also writes P[r] = v . d f / d ln A_r for the weight
 // vector v = vP (N): with q'_r = d q_r / d ln A_r (q_r for elementary and third-body
 // reactions; q_r (Pr/(1+Pr) - d ln F/d ln Pr) for fall-off reactions, whose A is that of
@@ -515,7 +516,8 @@ __device__ CellScalarsT<S> cell_rates(const DevMech& m, const Grp<G>& g, double 
     const S q = mfac * (kf * pf - kr * pr);
     w.q[r] = q;
     if (jac) {
-      S* o = scr + (size_t)r * 8;
+      S* o = scr + r;  // o[u * R]
+      const int R = m.R;
       S dH = w.hRT[p0] - w.hRT[a0];
       if (p1 >= 0) dH += w.hRT[p1];
       if (a1 >= 0) dH -= w.hRT[a1];
@@ -543,12 +545,12 @@ __device__ CellScalarsT<S> cell_rates(const DevMech& m, const Grp<G>& g, double 
           D = mfac * (kf * dpf - kr * dpr);
           DC = fma(D, w.C[j], DC);
         }
-        o[u] = D;
+        o[u * R] = D;
       }
-      o[4] = phi;
-      o[5] = DC;
-      o[6] = dqdT;
-      o[7] = dH * kRu * s.T;
+      o[4 * R] = phi;
+      o[5 * R] = DC;
+      o[6 * R] = dqdT;
+      o[7 * R] = dH * kRu * s.T;
       if (kP) {
         double gw = 0.0;  // sum over the species rows of nu_kr W_k v_Yk
 #pragma unroll
@@ -557,7 +559,7 @@ __device__ CellScalarsT<S> cell_rates(const DevMech& m, const Grp<G>& g, double 
           if (k >= 0) gw = fma(rd[3 + u] * m.sp[k * kSpDoubles], vP[1 + k], gw);
         }
         const S dq = fo ? q * (Pr / (1.0 + Pr) - dlF) : q;
-        P[r] = dq * s.inv_rho * (gw - vP[0] * (o[7] / s.cp));
+        P[r] = dq * s.inv_rho * (gw - vP[0] * (o[7 * R] / s.cp));
       }
     }
   }
@@ -603,7 +605,7 @@ __device__ void cell_jacobian(const DevMech& m, const Grp<G>& g, const CellScala
   // (row k, reaction r) pairs, v_kr = nu_kr phi_r.  The coefficients go to the stage-vector area
   // first (free while the Jacobian is built).
   S* v = w.pv;
-  for (int c = g.t; c < m.n_pairs; c += NT) v[c] = m.pr_nu[c] * scr[(size_t)m.pr_pd[c] * 8 + 4];
+  for (int c = g.t; c < m.n_pairs; c += NT) v[c] = m.pr_nu[c] * scr[4 * m.R + m.pr_pd[c]];
   g.sync();
   {
     const float invK = 1.0f / (float)K;
@@ -626,8 +628,8 @@ __device__ void cell_jacobian(const DevMech& m, const Grp<G>& g, const CellScala
     for (int e = m.sr_ptr[k]; e < m.sr_ptr[k + 1]; ++e) {
       const double nu = m.sr_nu[e];
       const int r = m.sr_idx[e];
-      zc = fma(nu, scr[(size_t)r * 8 + 5], zc);
-      dw = fma(nu, scr[(size_t)r * 8 + 6], dw);
+      zc = fma(nu, scr[5 * m.R + r], zc);
+      dw = fma(nu, scr[6 * m.R + r], dw);
     }
     w.zc[k] = zc;
     w.dwT[k] = dw;
@@ -688,6 +690,125 @@ __device__ void cell_jacobian(const DevMech& m, const Grp<G>& g, const CellScala
     const double Wk = m.sp[k * kSpDoubles];
     const double invWi = m.sp[i * kSpDoubles + 1];
     J[(1 + k) * N + 1 + i] = fma(-w.rowB[k], w.ccol[i], fma(-Wk * invWi, Z[k * N + i], w.rowA[k]));
+  }
+  g.sync();
+}
+
+// out = J^T v (J = d f / d phi at the state of the preceding cell_rates(jac) call, v a weight
+// vector of length N) without forming J.  With the notation of cell_jacobian (Z = d omega/dC on
+// the species rows k < K-1, a_k = W_k v_Yk, wq_k the enthalpy weights), the species block of J
+// contributes -ccol_i sum_k rowB_k v_Yk - (1/W_i) t_i + (1/W_K) t_K to column i, with
+// t_j = sum_k a_k Z_kj; the enthalpy row needs ZQ_j = sum_k wq_k Z_kj.  Both are weighted column
+// sums of Z: per reaction, A_r = sum_rows nu_kr a_k and B_r = sum_rows nu_kr wq_k, then
+// t_j = sum over the reactions with slot species j of (dq_r/dC_j) A_r + sum_pd phi_r A_r eff_rj
+// (and the same with B for ZQ).  Cost O(R + contributions + n_pd K), no N x N scratch.
+// ab: 2 R + 2 n_pd entries of scratch, tz: 2 K; out: N entries.
+template <int G, class S>
+__device__ void cell_jacobian_vjp(const DevMech& m, const Grp<G>& g, const CellScalarsT<S>& s, const S* f,
+                                  const EvalMem<S>& w, const S* scr, const double* v, S* ab, S* tz, S* out) {
+  constexpr int NT = Grp<G>::NT;
+  const int K = m.K, R = m.R, d = K - 1, npd = m.n_pd;
+  const double invWd = m.sp[d * kSpDoubles + 1];
+  const S RuT = kRu * s.T;
+  S* Ar = ab;
+  S* Br = ab + R;
+  S* fA = ab + 2 * R;
+  S* fB = fA + npd;
+  S* t = tz;
+  S* zq = tz + K;
+  // species: enthalpy weights and the gathers of sum_j dq/dC_j C_j and dq/dT
+  for (int k = g.t; k < d; k += NT) {
+    S zc = cst<S>(0.0), dw = cst<S>(0.0);
+    for (int e = m.sr_ptr[k]; e < m.sr_ptr[k + 1]; ++e) {
+      const double nu = m.sr_nu[e];
+      const int r = m.sr_idx[e];
+      zc = fma(nu, scr[5 * R + r], zc);
+      dw = fma(nu, scr[6 * R + r], dw);
+    }
+    w.zc[k] = zc;
+    w.dwT[k] = dw;
+    w.wq[k] = RuT * (w.hRT[k] - w.hRT[d] * m.sp[k * kSpDoubles] * invWd);
+  }
+  g.sync();
+  // per-reaction row weights
+  for (int r = g.t; r < R; r += NT) {
+    const int* ii = m.rxi + r * kRxInts;
+    const double* rd = m.rxd + r * kRxDoubles;
+    double a = 0.0;
+    S b = cst<S>(0.0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = ii[8 + u];
+      if (k >= 0) {
+        a = fma(rd[3 + u] * m.sp[k * kSpDoubles], v[1 + k], a);
+        b = fma(rd[3 + u], w.wq[k], b);
+      }
+    }
+    Ar[r] = cst<S>(a);
+    Br[r] = b;
+    if (r < npd) {
+      const S phi = scr[4 * R + r];
+      fA[r] = phi * a;
+      fB[r] = phi * b;
+    }
+  }
+  g.sync();
+  // weighted column sums t_j and ZQ_j, with sum_j ZQ_j C_j and sum_j cp_j omega_j
+  S zqc = cst<S>(0.0), cpw = cst<S>(0.0);
+  for (int j = g.t; j < K; j += NT) {
+    S tj = cst<S>(0.0), qj = cst<S>(0.0);
+    for (int e = m.cl_ptr[j]; e < m.cl_ptr[j + 1]; ++e) {
+      const S D = scr[m.cl_src[e]];
+      const int r = m.cl_rx[e];
+      tj = fma(D, Ar[r], tj);
+      qj = fma(D, Br[r], qj);
+    }
+    for (int p = 0; p < npd; ++p) {
+      const double ej = m.eff[(size_t)p * K + j];
+      tj = fma(ej, fA[p], tj);
+      qj = fma(ej, fB[p], qj);
+    }
+    t[j] = tj;
+    zq[j] = qj;
+    zqc = fma(qj, w.C[j], zqc);
+    cpw = fma(w.cpR[j], w.omega[j], cpw);
+  }
+  // species sums: sum_k a_k (zc_k - omega_k), sum_k wq_k dwT_k, and the temperature column
+  S sB = cst<S>(0.0), dqt = cst<S>(0.0), sT = cst<S>(0.0);
+  for (int k = g.t; k < d; k += NT) {
+    const double Wk = m.sp[k * kSpDoubles];
+    const double ak = Wk * v[1 + k];
+    sB = fma(ak, w.zc[k] - w.omega[k], sB);
+    dqt = fma(w.wq[k], w.dwT[k], dqt);
+    // -J[1+k][0] (stored-negated form of cell_jacobian) times v_Yk
+    const S nj = -(Wk * s.inv_rho * (w.dwT[k] - w.zc[k] * s.invT) + f[1 + k] * s.invT);
+    sT = fma(nj, v[1 + k], sT);
+  }
+  g.sum2(zqc, cpw);
+  g.sum2(sB, dqt);
+  sT = g.sum(sT);
+  cpw = cpw * kRu;
+  sB = sB * s.inv_rho;
+  g.sync();
+  const S inv_rhocp = s.inv_rho / s.cp;
+  const S inv_cp = 1.0 / s.cp;
+  const S fT = s.fT;
+  const S sA = invWd * t[d];
+  const S ZQd = zq[d];
+  const S cpd = w.cpR[d] * invWd;
+  const double v0 = v[0];
+  for (int i = g.t; i < d; i += NT) {
+    const double invWi = m.sp[i * kSpDoubles + 1];
+    const S ci = -s.Wbar * (invWi - invWd);
+    const S dQdY = s.rho * (invWi * zq[i] - invWd * ZQd) + zqc * ci;
+    const S dcpdY = (w.cpR[i] * invWi - cpd) * kRu;
+    const S nj0 = fma(dQdY, inv_rhocp, fT * (ci + dcpdY * inv_cp));  // -J[0][1+i]
+    const S blk = sA - ci * sB - invWi * t[i];                           // sum_k -J[1+k][1+i] v_Yk
+    out[1 + i] = -fma(nj0, v0, blk);
+  }
+  if (g.t == 0) {
+    const S nj00 = (cpw + dqt - zqc * s.invT) * inv_rhocp + fT * (-s.invT + s.dcp_dT * inv_cp);
+    out[0] = -fma(nj00, v0, sT);
   }
   g.sync();
 }

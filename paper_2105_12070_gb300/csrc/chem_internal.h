@@ -57,6 +57,11 @@ struct HostMech {
   std::vector<double> pr_nu;
   std::vector<int> pr_row;             // row of each (row, reaction) pair
   std::vector<int> pr_rows;            // rows with pairs, shortest lists first
+  // Column lists (products with J^T): for species column j, the per-reaction scratch indices
+  // of dq/dC_j and their reactions
+  std::vector<int> cl_ptr;             // [K + 1]
+  std::vector<int> cl_src;
+  std::vector<int> cl_rx;
 };
 
 // Parse the mechanism text file; false + message on error.
@@ -88,6 +93,9 @@ struct DevMech {
   const int* pr_rows;
   int n_pairs, n_prows;
   const int* order;  // device reaction index -> file reaction index
+  const int* cl_ptr;
+  const int* cl_src;
+  const int* cl_rx;
 };
 
 }  // namespace chemgpu

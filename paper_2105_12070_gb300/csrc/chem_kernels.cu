@@ -669,6 +669,9 @@ int chem_load_mechanism(const char* path, chem_mech** out) {
   const size_t o_prr = place(std::max<size_t>(1, h.pr_row.size()) * sizeof(int));
   const size_t o_prs = place(std::max<size_t>(1, h.pr_rows.size()) * sizeof(int));
   const size_t o_ord = place(h.order.size() * sizeof(int));
+  const size_t o_clp = place(h.cl_ptr.size() * sizeof(int));
+  const size_t o_cls = place(std::max<size_t>(1, h.cl_src.size()) * sizeof(int));
+  const size_t o_clr = place(std::max<size_t>(1, h.cl_rx.size()) * sizeof(int));
   const size_t total = off;
   std::vector<char> img(total, 0);
   auto put = [&](size_t o, const void* src, size_t bytes) { if (bytes) std::memcpy(img.data() + o, src, bytes); };
@@ -692,6 +695,9 @@ int chem_load_mechanism(const char* path, chem_mech** out) {
   put(o_prr, h.pr_row.data(), h.pr_row.size() * sizeof(int));
   put(o_prs, h.pr_rows.data(), h.pr_rows.size() * sizeof(int));
   put(o_ord, h.order.data(), h.order.size() * sizeof(int));
+  put(o_clp, h.cl_ptr.data(), h.cl_ptr.size() * sizeof(int));
+  put(o_cls, h.cl_src.data(), h.cl_src.size() * sizeof(int));
+  put(o_clr, h.cl_rx.data(), h.cl_rx.size() * sizeof(int));
   e = cudaMalloc(&m->dbuf, total);
   if (e == cudaSuccess) e = cudaMemcpy(m->dbuf, img.data(), total, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&m->d_totals, 4 * sizeof(unsigned long long));
@@ -725,6 +731,9 @@ int chem_load_mechanism(const char* path, chem_mech** out) {
   d.pr_row = reinterpret_cast<const int*>(b + o_prr);
   d.pr_rows = reinterpret_cast<const int*>(b + o_prs);
   d.order = reinterpret_cast<const int*>(b + o_ord);
+  d.cl_ptr = reinterpret_cast<const int*>(b + o_clp);
+  d.cl_src = reinterpret_cast<const int*>(b + o_cls);
+  d.cl_rx = reinterpret_cast<const int*>(b + o_clr);
   d.n_pairs = (int)h.pr_pd.size();
   d.n_prows = (int)h.pr_rows.size();
   if (d.n_pairs > 8 * (((h.K + 1) / 2) * 2)) {

@@ -64,8 +64,9 @@ struct FileReaction {
 
 // Gather plan of the Jacobian's mass-action part and the row lists of its efficiency part, for
 // the species rows k < K-1 (the enthalpy row follows from them, see the kernels).
-// Per-reaction scratch layout (see the kernels): [0..3] dq/dC at the distinct slot species,
-// [4] phi, [5] sum_j dq/dC_j C_j, [6] dq/dT, [7] reaction enthalpy.
+// Per-reaction scratch layout (see the kernels): 8 rows of R values, scr[u * R + r] with u =
+// 0..3 dq/dC at the distinct slot species, 4 phi, 5 sum_j dq/dC_j C_j, 6 dq/dT, 7 reaction
+// enthalpy (rows, so that the threads of consecutive reactions touch consecutive words).
 void build_jacobian_plan(HostMech& m) {
   const int K = m.K, d = K - 1;
   struct Contrib { int dst, src, src2; double coef; };
@@ -78,7 +79,7 @@ void build_jacobian_plan(HostMech& m) {
       for (int rs = 0; rs < 4; ++rs) {
         const int row = ii[8 + rs];
         if (row < 0) continue;
-        cs.push_back({row * K + col, r * 8 + u, -1, (double)ii[12 + rs]});
+        cs.push_back({row * K + col, u * m.R + r, -1, (double)ii[12 + rs]});
       }
     }
   }
@@ -128,6 +129,19 @@ void build_jacobian_plan(HostMech& m) {
   std::stable_sort(m.pr_rows.begin(), m.pr_rows.end(), [&](int a, int b) {
     return (m.pr_ptr[a + 1] - m.pr_ptr[a]) < (m.pr_ptr[b + 1] - m.pr_ptr[b]);
   });
+  // column lists for products with J^T: for each species column j, the scratch entries
+  // dq/dC_j (u * R + r) of the reactions that have j among their distinct slot species
+  m.cl_ptr.assign(K + 1, 0);
+  m.cl_src.clear(); m.cl_rx.clear();
+  for (int j = 0; j < K; ++j) {
+    m.cl_ptr[j] = (int)m.cl_src.size();
+    for (int r = 0; r < m.R; ++r) {
+      const int* ii = &m.rxi[(size_t)r * kRxInts];
+      for (int u = 0; u < 4; ++u)
+        if (ii[4 + u] == j) { m.cl_src.push_back(u * m.R + r); m.cl_rx.push_back(r); }
+    }
+  }
+  m.cl_ptr[K] = (int)m.cl_src.size();
 }
 
 }  // namespace
