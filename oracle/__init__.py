@@ -69,7 +69,7 @@ def _load():
                                                _dp]
             lib.oracle_integrate.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, _dp, _dp,
                                              ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _ip, _ip, _ip,
-                                             ctypes.c_int, ctypes.c_int]
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.oracle_ros_coefficients.argtypes = [_dp]
             lib.oracle_opcount.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _dp, _lp]
             lib.oracle_integrate_record.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, ctypes.c_double,
@@ -150,8 +150,10 @@ class OracleMechanism:
         return J
 
     def integrate(self, p_Pa: float, T, Y, dt: float, rtol: float = 1e-6, atol: float = 1e-10, h_inout=None,
-                  max_steps: int = 100000, nthreads: int = 1):
-        """Returns (T, Y, status, steps, rejects); inputs are not modified; h_inout is updated in place."""
+                  max_steps: int = 100000, nthreads: int = 1, solver: str = "rosenbrock"):
+        """Returns (T, Y, status, steps, rejects); inputs are not modified; h_inout is updated in place.
+        solver: "rosenbrock" (the 4-stage method) or "seulex" (extrapolated linearly implicit Euler)."""
+        solver_id = {"rosenbrock": 0, "seulex": 1}[solver]
         T = _f64(T).copy()
         Y = _f64(Y).copy()
         n = T.shape[0]
@@ -162,7 +164,7 @@ class OracleMechanism:
             assert h_inout.dtype == np.float64 and h_inout.flags.c_contiguous and h_inout.shape == (n,)
         self._lib.oracle_integrate(self._h, float(p_Pa), n, _p(T), _p(Y), float(dt), float(rtol), float(atol),
                                    _p(h_inout), _p(status, _ip), _p(steps, _ip), _p(rej, _ip), int(max_steps),
-                                   int(nthreads))
+                                   int(nthreads), solver_id)
         return T, Y, status, steps, rej
 
     def integrate_record(self, p_Pa: float, phi, dt: float, rtol: float = 1e-6, atol: float = 1e-10,

@@ -655,6 +655,167 @@ static int integrate_cell(const Mech& m, double p, double* phi, double dt, doubl
   return status;
 }
 
+// ----------------------------------------------------------------------------------------------
+// Seulex: the linearly implicit Euler method with extrapolation (the paper's integrator,
+// Sec. 2.3, following Hairer & Wanner, Solving ODEs II, Sec. IV.9).  One macro step of size H
+// from y, with J = J(y):
+//   column j = 1..: n_j = j sub-steps of h = H/n_j,  (I - h J)(y_{i+1} - y_i) = h f(y_i),
+//   T_{j,1} = y_{n_j};  T_{j,l} = T_{j,l-1} + (T_{j,l-1} - T_{j-1,l-1}) / (n_j/n_{j-l+1} - 1)
+//   err_j = max_i |T_{j,j} - T_{j,j-1}| / (atol + rtol max(|y_i|, |T_{j,j,i}|)),
+//   fac_j = min(4, max(0.02, 0.94 err_j^(-1/j))).
+// With target column k (2 <= k <= kmax-1) the columns up to k+1 are computed as needed:
+//   j = k-1 (j >= 2): accept if err <= 1;
+//   j = k:            accept if err <= 1; give up if err > (n_{k+1} / n_1)^2;
+//   j = k+1:          accept if err <= 1, else give up.
+// (Column k-1 never gives up early: on linear test problems at tight tolerances a give-up there
+// predicted from the square of the step-number ratio rejected steps that column k accepts, and
+// the controller cycled at low order.)
+// Accepted at column c: y <- T_{c,c}; the next target and step minimise the work per unit step
+// w_j = A_j / (H fac_j), A_j the cost of columns 1..j in rate-evaluation units (Jacobian 2.5,
+// LU 2, rate evaluation 1, solve 0.2):
+//   c = 2:      k = 3, H <- H fac_2 A_3/A_2 (H fac_2 after a rejection);
+//   2 < c <= k: k = c, or c-1 if w_{c-1} < 0.8 w_c, or c+1 if c = k and w_c < 0.9 w_{c-1};
+//               H <- H fac_min(k,c) (times A_k/A_c when k > c);
+//   c = k+1:    k = c-1, or c if w_c < 0.9 w_{c-1}; H <- H fac_k;
+//   after a rejection H does not grow and k <= c.
+// Given up: H <- H min(fac_m, 1/2) with m = min(k, last column), k <- m (J is kept).  A singular
+// iteration matrix or a non-finite error gives up with H <- H/5.  Cold start H = 0.01 dt, k = 2.
+// The last step is clipped to end at dt; h_inout carries the unclipped proposal over.
+struct Seulex {
+  static constexpr int kmax = 8;
+  double A[kmax + 1];
+  Seulex() {
+    const double cJ = 2.5, cLU = 2.0, cf = 1.0, cs = 0.2;
+    A[0] = 0.0;
+    A[1] = cJ + cLU + 1.0 * (cs + cf);
+    for (int j = 2; j <= kmax; ++j) A[j] = A[j - 1] + cLU + j * cs + (j - 1) * cf;
+  }
+  static int n(int j) { return j; }
+};
+
+static int integrate_cell_seulex(const Mech& m, double p, double* phi, double dt, double rtol, double atol,
+                                 double* h_io, int max_steps, CellStats& cs) {
+  const int N = m.K;
+  if (!(std::isfinite(phi[0]) && phi[0] > 0.0)) return kBadInput;
+  for (int i = 1; i < N; ++i)
+    if (!std::isfinite(phi[i])) return kBadInput;
+  Seulex c;
+  const int kmax = Seulex::kmax;
+  std::vector<double> y(phi, phi + N), f0(N), fi(N), yi(N), d(N), J((size_t)N * N), W((size_t)N * N), q(N),
+      qn(N);
+  std::vector<std::vector<double>> T(kmax + 1, std::vector<double>(N));  // T[l] = current row's T_{.,l}
+  std::vector<int> piv(N);
+  double H = (h_io && *h_io > 0.0) ? std::min(*h_io, dt) : 0.01 * dt;
+  double t = 0.0, H_next_unclipped = H;
+  int k = 2;
+  bool need_jac = true, last_rejected = false;
+  int status = kOk;
+  for (int attempt = 0;; ++attempt) {
+    if (attempt >= max_steps) { status = kMaxSteps; break; }
+    if (H_next_unclipped < 1e-14 * dt) { status = kHUnderflow; break; }
+    if (need_jac) {
+      jacobian(m, p, y.data(), f0.data(), J.data());
+      cs.f_evals++;
+      need_jac = false;
+    }
+    double err[kmax + 2], fac[kmax + 2];
+    int accepted = 0, last = 0;
+    bool bad = false;
+    for (int j = 1; j <= k + 1; ++j) {
+      last = j;
+      const double h = H / Seulex::n(j);
+      for (size_t e = 0; e < (size_t)N * N; ++e) W[e] = -h * J[e];
+      for (int i = 0; i < N; ++i) W[(size_t)i * N + i] += 1.0;
+      cs.lu++;
+      if (!lu_factor(N, W.data(), piv.data())) { bad = true; break; }
+      yi = y;
+      for (int s = 0; s < Seulex::n(j); ++s) {
+        if (s == 0) {
+          fi = f0;
+        } else {
+          RateState<double> st;
+          rates(m, p, yi.data(), fi.data(), st);
+          cs.f_evals++;
+        }
+        for (int i = 0; i < N; ++i) d[i] = h * fi[i];
+        lu_solve(N, W.data(), piv.data(), d.data());
+        for (int i = 0; i < N; ++i) yi[i] += d[i];
+      }
+      // Aitken-Neville: T holds row j-1 in T[1..j-1]; build row j, overwriting as we go
+      q = yi;
+      for (int l = 2; l <= j; ++l) {
+        const double r = (double)Seulex::n(j) / (double)Seulex::n(j - l + 1);
+        for (int i = 0; i < N; ++i) qn[i] = q[i] + (q[i] - T[l - 1][i]) / (r - 1.0);
+        T[l - 1] = q;
+        q = qn;
+      }
+      T[j] = q;
+      if (j < 2) continue;
+      double e = 0.0;
+      for (int i = 0; i < N; ++i) {
+        const double sc = atol + rtol * std::max(std::fabs(y[i]), std::fabs(T[j][i]));
+        const double r = std::fabs(T[j][i] - T[j - 1][i]) / sc;
+        if (!(r <= e)) e = r;  // propagates NaN
+      }
+      if (!std::isfinite(e)) { bad = true; break; }
+      err[j] = e;
+      fac[j] = (e > 0.0) ? std::min(4.0, std::max(0.02, 0.94 * std::pow(e, -1.0 / j))) : 4.0;
+      const double n1 = Seulex::n(1), nk1 = Seulex::n(k + 1);
+      if (j == k - 1) {
+        if (e <= 1.0) { accepted = j; break; }
+      } else if (j == k) {
+        if (e <= 1.0) { accepted = j; break; }
+        if (e > (nk1 / n1) * (nk1 / n1)) break;
+      } else if (j == k + 1) {
+        if (e <= 1.0) accepted = j;
+        break;
+      }
+    }
+    if (accepted) {
+      const int a = accepted;
+      t = (H >= dt - t) ? dt : t + H;
+      y = T[a];
+      cs.steps++;
+      need_jac = true;
+      auto w = [&](int j) { return c.A[j] / (H * fac[j]); };
+      int knew;
+      double Hn;
+      if (a == 2) {
+        knew = 3;
+        Hn = H * fac[2] * (last_rejected ? 1.0 : c.A[3] / c.A[2]);
+      } else if (a <= k) {
+        knew = a;
+        if (w(a - 1) < 0.8 * w(a)) knew = a - 1;
+        else if (a == k && w(a) < 0.9 * w(a - 1)) knew = a + 1;
+        Hn = H * fac[std::min(knew, a)] * (knew > a ? c.A[knew] / c.A[a] : 1.0);
+      } else {
+        knew = a - 1;
+        if (w(a) < 0.9 * w(a - 1)) knew = a;
+        Hn = H * fac[knew];
+      }
+      if (last_rejected) { Hn = std::min(Hn, H); knew = std::min(knew, a); }
+      k = std::max(2, std::min(knew, kmax - 1));
+      last_rejected = false;
+      H_next_unclipped = Hn;
+      if (t >= dt) break;
+    } else {
+      cs.rejects++;
+      last_rejected = true;
+      if (bad) {
+        H_next_unclipped = H * 0.2;
+      } else {
+        const int mcol = std::min(k, last);
+        H_next_unclipped = H * std::min(fac[mcol], 0.5);
+        k = std::max(2, mcol);
+      }
+    }
+    H = std::min(H_next_unclipped, dt - t);
+  }
+  for (int i = 0; i < N; ++i) phi[i] = y[i];
+  if (h_io) *h_io = H_next_unclipped;
+  return status;
+}
+
 // One Rosenbrock step of size h from y (no error control): the same classical-form formulas as
 // integrate_cell, templated so that the dual-number instance gives the tangent-linear step
 // (forward sensitivities through the discrete method with the step size frozen).
@@ -836,8 +997,10 @@ int oracle_jacobian_cs(void* h, double p_Pa, double T, const double* Y, double s
 
 // Integrate n cells over dt.  T[n] and Y[K][n] are updated in place (Y_K = 1 - sum of the
 // others on output).  h_inout[n] may be NULL.  status[n], steps[n], rejects[n] may be NULL.
+// solver 0 = Rosenbrock (integrate_cell), 1 = Seulex (integrate_cell_seulex).
 int oracle_integrate(void* h, double p_Pa, int64_t n, double* T, double* Y, double dt, double rtol, double atol,
-                     double* h_inout, int32_t* status, int32_t* steps, int32_t* rejects, int max_steps, int nthreads) {
+                     double* h_inout, int32_t* status, int32_t* steps, int32_t* rejects, int max_steps, int nthreads,
+                     int solver) {
   Mech* m = static_cast<Mech*>(h);
   const int K = m->K, N = K;
   if (nthreads < 1) nthreads = 1;
@@ -850,8 +1013,11 @@ int oracle_integrate(void* h, double p_Pa, int64_t n, double* T, double* Y, doub
       phi[0] = T[c];
       for (int k = 0; k < K - 1; ++k) phi[1 + k] = Y[(size_t)k * n + c];
       CellStats cs;
-      int st = integrate_cell(*m, p_Pa * 10.0, phi.data(), dt, rtol, atol, h_inout ? &h_inout[c] : nullptr,
-                              max_steps, cs);
+      int st = (solver == 1)
+                   ? integrate_cell_seulex(*m, p_Pa * 10.0, phi.data(), dt, rtol, atol,
+                                           h_inout ? &h_inout[c] : nullptr, max_steps, cs)
+                   : integrate_cell(*m, p_Pa * 10.0, phi.data(), dt, rtol, atol, h_inout ? &h_inout[c] : nullptr,
+                                    max_steps, cs);
       T[c] = phi[0];
       double ysum = 0.0;
       for (int k = 0; k < K - 1; ++k) { Y[(size_t)k * n + c] = phi[1 + k]; ysum += phi[1 + k]; }
