@@ -40,6 +40,11 @@ OPCOUNT_FILE = os.path.join(ROOT, "tests", "golden", "opcount_mech53.json")
 # FLOPs per operation: add, mul and div count 1; an exp or log counts its cost in FMA flops
 # (measured FP64 pipe throughput of exp and log relative to DFMA on GB300: 17 and 31 DFMA)
 FLOP_WEIGHTS = {"add": 1, "mul": 1, "div": 1, "exp": 2 * 17, "log": 2 * 31}
+# DRAM bytes (read + write) of the integrate kernel per cell, from the ncu capture summarised in
+# profiles/integrate_kernel_mech53_shear.md (608-cell slice of the shear-layer field: 1.143 MB
+# read, 0 B written); the kernel's DRAM traffic is the per-cell state and the tables, so it scales
+# with the cells of a launch
+TRAFFIC_BYTES_PER_CELL = 1143296 / 608
 
 
 def _env_int(name, default):
@@ -56,6 +61,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--solver", choices=["rosenbrock", "seulex"], default="rosenbrock",
+                    help="integrator: the 4-stage Rosenbrock method or the paper's Seulex")
     ap.add_argument("--cells", type=int, default=0, help="cells per rank (0 = the full 65536-cell field)")
     ap.add_argument("--dt", type=float, default=0.0, help="override the CFD time step (profiling small cases)")
     ap.add_argument("--workload", choices=["shear", "uneven", "adjoint"], default="shear",
@@ -65,6 +72,8 @@ def parse_args():
                     help="also time one launch per batch of this many cells (static assignment) against the queue")
     ap.add_argument("--autotune", action="store_true", help="pick warps/cell and cells/CTA with the autotuner first")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--warm-start", action="store_true",
+                    help="also time the next CFD step: from the state at dt, with the carried-over sub-step h")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0 = auto)")
     return ap.parse_args()
 
@@ -337,11 +346,13 @@ def main():
     status = torch.zeros(n_total, dtype=torch.int32, device="cuda")
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     prec = chem.CHEM_PREC_MIXED if args.precision == "mixed" else chem.CHEM_PREC_FP64
+    solver = chem.CHEM_SOLVER_SEULEX if args.solver == "seulex" else chem.CHEM_SOLVER_ROSENBROCK
     if args.autotune:
         from paper_2105_12070_gb300 import autotune
         opts = autotune.autotune(mech, w["p_Pa"], w["T"], w["Y"], w["dt"], precision=prec)
+        opts.solver = solver
     else:
-        opts = chem.default_opts(precision=prec)
+        opts = chem.default_opts(precision=prec, solver=solver)
     opts.use_graph = 1
     stream = torch.cuda.current_stream()
 
@@ -383,7 +394,8 @@ def main():
     cells = n_total * world * args.steps
     value = cells / (kern_ms / 1e3)
     e2e_value = cells / (e2e_ms / 1e3)
-    flops, per = algorithmic_flops(steps_np, rej_np) if mech.K == 53 else (float("nan"), {"per_attempt": None,
+    rosen = solver == chem.CHEM_SOLVER_ROSENBROCK
+    flops, per = algorithmic_flops(steps_np, rej_np) if (mech.K == 53 and rosen) else (float("nan"), {"per_attempt": None,
                                                                                       "per_accepted": None})
     achieved = flops / (kern_ms / 1e3 / args.steps) / 1e12  # TFLOP/s, one launch
     peak = fp64_peak_tflops()
@@ -393,20 +405,48 @@ def main():
         "vs_baseline": None, "dtype": "f64" if prec == chem.CHEM_PREC_FP64 else "f64+f32", "data": "synthetic",
         "config": {"workload": w["name"], "cells": n_total, "species": mech.K, "reactions": mech.R, "dt_s": w["dt"],
                    "p_atm": w["p_Pa"] / 101325.0, "rtol": w["rtol"], "atol": w["atol"], "precision": args.precision,
+                   "solver": args.solver,
                    "warps_per_cell": opts.warps_per_cell, "cells_per_cta": opts.cells_per_cta, "cuda_graph": True,
                    "scheduling": "persistent kernel + device work queue", "l2": "flushed between steps (256 MiB write)",
                    "start": "cold (every step from the initial field)"},
         "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": int(T_host.numel() * 8 + Y_host.numel() * 8),
                 "d2h_bytes_per_step": int(T_out.numel() * 8 + Y_out.numel() * 8)},
         "gpu_launches": 1 * args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak["tflops"], "unit": "TFLOP/s",
-                     "frac": achieved / peak["tflops"], "traffic": None, "peak_source": peak["source"],
+        "roofline": {"bound": "alu", "achieved": achieved if np.isfinite(achieved) else None,
+                     "peak": peak["tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / peak["tflops"] if np.isfinite(achieved) else None,
+                     "traffic": (TRAFFIC_BYTES_PER_CELL * n_total
+                                 if (mech.K == 53 and prec == chem.CHEM_PREC_FP64 and rosen) else None),
+                     "peak_source": peak["source"],
                      "flops_per_attempt": per["per_attempt"], "flops_per_accepted_step": per["per_accepted"]},
         "clocks": clk,
         "cells_status": {str(k): int(v) for k, v in zip(*np.unique(st_np, return_counts=True))},
         "steps_per_cell": {"mean": float(steps_np.mean()), "max": int(steps_np.max()),
                            "rejects_mean": float(rej_np.mean())},
     }
+    if args.warm_start:
+        # the next CFD step of the same field: an untimed cold call leaves T, Y at dt and the
+        # controller's proposal in h; the timed call continues from there (Sec. 2.3: the previous
+        # sub-step is the first guess of the next interval)
+        hbuf = torch.zeros(n_total, dtype=torch.float64, device="cuda")
+        T.copy_(T_host)
+        Y.copy_(Y_host)
+        chem.chem_integrate(mech, w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], h_inout=hbuf, status=status,
+                            opts=opts)
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        chem.chem_integrate(mech, w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], h_inout=hbuf, status=status,
+                            opts=opts)
+        e1.record(stream)
+        e1.synchronize()
+        wms = e0.elapsed_time(e1)
+        chem.chem_last_cell_counters(mech, steps, rej)
+        wst = steps.cpu().numpy()
+        line["warm_start"] = {"value": n_total / (wms / 1e3), "unit": "cells/s", "ms_per_step": wms,
+                              "steps_per_cell_mean": float(wst.mean()), "steps_per_cell_max": int(wst.max()),
+                              "cells_status": {str(k): int(v) for k, v in
+                                               zip(*np.unique(status.cpu().numpy(), return_counts=True))}}
     if args.batch_cells > 0:
         # one launch per batch of consecutive cells, static assignment inside each launch
         bopts = chem.default_opts(precision=prec, use_queue=0, batch_cells=args.batch_cells,

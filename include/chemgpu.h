@@ -48,6 +48,12 @@ extern "C" {
                                     the cell stops at its last recorded step */
 
 /* precision of the linear solves inside the Rosenbrock stages */
+/* integrators (chem_opts.solver) */
+#define CHEM_SOLVER_ROSENBROCK 0 /* 4-stage L-stable Rosenbrock method, order 4(3) (default) */
+#define CHEM_SOLVER_SEULEX 1     /* the paper's Seulex (Sec. 2.3): linearly implicit Euler with
+                                    extrapolation, harmonic step-number sequence, up to 8 columns,
+                                    order and step chosen by work per unit step; FP64 only */
+
 #define CHEM_PREC_FP64 0   /* FP64 LU and substitutions */
 #define CHEM_PREC_MIXED 1  /* FP32 LU + FP64-residual iterative refinement; rates, Kc, error
                               norm, step control and state update stay FP64 */
@@ -69,6 +75,7 @@ typedef struct {
   int batch_cells;    /* > 0: split the cells into consecutive batches of this many cells, one
                          kernel launch per batch (the one-launch-per-batch comparison of the
                          persistent queue); 0 (default): one launch for all cells */
+  int solver;         /* CHEM_SOLVER_ROSENBROCK (default) or CHEM_SOLVER_SEULEX */
 } chem_opts;
 
 typedef struct {

@@ -69,6 +69,7 @@ struct IntegrateArgs {
   int refine_sweeps;  // refinement sweeps per stage solve (mixed)
   double* rec;        // record mode: checkpoint of every accepted step (NULL: off)
   int rec_cap;        // checkpoints per cell
+  int solver;         // CHEM_SOLVER_*
 };
 
 // ------------------------------------------------------------------------------------------
@@ -356,6 +357,202 @@ __global__ void __launch_bounds__(256, 1) integrate_kernel(DevMech m, Plan plan,
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Seulex (the paper's integrator, Sec. 2.3; Hairer & Wanner IV.9): the linearly implicit Euler
+// method with extrapolation.  Per macro step H from y with J = J(y): column j takes n_j = j
+// sub-steps of h = H/j, (I/h - J) d = f(y_i), y_{i+1} = y_i + d (one LU of I/h - J per column),
+// T_{j,1} = y_{n_j}; Aitken-Neville T_{j,l} = T_{j,l-1} + (T_{j,l-1} - T_{j-1,l-1}) /
+// (n_j/n_{j-l+1} - 1); err_j = max norm of T_{j,j} - T_{j,j-1} (scale atol + rtol max(|y|,
+// |T_jj|)), fac_j = min(4, max(0.02, 0.94 err_j^(-1/j))).  Target column k in [2, kmax-1]:
+// accept at column k-1 or k if err <= 1, give up at k if err > (n_{k+1}/n_1)^2, decide at k+1.
+// The next target and step minimise the work per unit step A_j / (H fac_j), A_j the cost of
+// columns 1..j in rate-evaluation units (Jacobian 2.5, LU 2, rate evaluation 1, solve 0.2).  A
+// give-up keeps J and shrinks H by min(fac, 1/2); a singular matrix or a non-finite error by 1/5.
+// The tableau row lives in eight of the cell's vectors and is updated element by element.
+constexpr int kSeulexKmax = 8;
+
+__device__ inline double seulex_work(int j) {
+  // A_1 = 2.5 + 2 + (0.2 + 1); A_j = A_{j-1} + 2 + 0.2 j + (j - 1)
+  double a = 2.5 + 2.0 + 1.2;
+  for (int i = 2; i <= j; ++i) a += 2.0 + 0.2 * i + (i - 1);
+  return a;
+}
+
+template <int G>
+__global__ void __launch_bounds__(256, 1) seulex_kernel(DevMech m, Plan plan, IntegrateArgs a) {
+  extern __shared__ double smem[];
+  Grp<G> g;
+  g.t = threadIdx.x % Grp<G>::NT;
+  g.gid = threadIdx.x / Grp<G>::NT;
+  g.parity = 0;
+  CellMem w = carve(smem + (size_t)g.gid * plan.total, plan);
+  g.red = w.red;
+  constexpr int NT = Grp<G>::NT;
+  constexpr int kmax = kSeulexKmax;
+  const int N = m.N, K = m.K;
+  const int groups_per_cta = blockDim.x / NT;
+  const int64_t ngroups = (int64_t)gridDim.x * groups_per_cta;
+  int64_t static_next = (int64_t)blockIdx.x * groups_per_cta + g.gid;
+  // tableau row T_1..T_8 in the vectors u0..u3, err, res and the two last ones (vector slots
+  // 4..8 and 11..13 of the plan), addressed arithmetically so that nothing goes to local memory
+  const int n2 = (int)(w.ynew - w.y);
+  auto tab = [&](int l) { return w.y + (size_t)(l + 3 + (l >= 6 ? 2 : 0)) * n2; };
+  double* yi = w.ynew;
+  double* fi = w.fs;
+  double* d = w.rhs;
+  for (;;) {
+    const int64_t cell = next_cell(a, g, w, static_next, ngroups);
+    if (cell < 0) break;
+    int bad = 0;
+    for (int i = g.t; i < N; i += NT) {
+      const double v = (i == 0) ? a.T[cell] : a.Y[(size_t)(i - 1) * a.ncells + cell];
+      w.y[i] = v;
+      bad |= !isfinite(v);
+    }
+    bad = (g.sum((double)bad) > 0.0) || !(a.T[cell] > 0.0);
+    int status = bad ? CHEM_CELL_BAD_INPUT : CHEM_CELL_OK;
+    int nsteps = 0, nrej = 0;
+    double H_next = 0.01 * a.dt;
+    if (a.h_inout) {
+      const double h0 = a.h_inout[cell];
+      if (h0 > 0.0) H_next = fmin(h0, a.dt);
+    }
+    double t = 0.0, H = H_next;
+    int k = 2;
+    bool need_jac = true, last_rej = false;
+    g.sync();
+    for (int attempt = 0; status == CHEM_CELL_OK; ++attempt) {
+      if (attempt >= a.max_steps) { status = CHEM_CELL_MAX_STEPS; break; }
+      if (H_next < 1e-14 * a.dt) { status = CHEM_CELL_H_UNDERFLOW; break; }
+      if (need_jac) {
+        const CellScalars s0 = cell_rates(m, g, a.p, w.y, w.f0, eval_mem(w), w.A, true);
+        cell_jacobian(m, g, s0, w.f0, eval_mem(w), w.A, w.B);
+        need_jac = false;
+      }
+      double fac_cur = 0.2, fac_prv = 0.2;  // fac of the last column computed and of the one before
+      int accepted = 0, last = 0;
+      bool badstep = false;
+      for (int j = 1; j <= k + 1; ++j) {
+        last = j;
+        const double gh = (double)j / H;  // 1/h
+        for (int e = g.t; e < N * N; e += NT) w.B[e] = w.A[e];
+        g.sync();
+        for (int i = g.t; i < N; i += NT) w.B[i * N + i] += gh;
+        g.sync();
+        if (!cell_lu<G, double>(g, w.B, N, w.piv, w.perm, w.invdiag)) { badstep = true; break; }
+        for (int i = g.t; i < N; i += NT) yi[i] = w.y[i];
+        for (int sub = 0; sub < j; ++sub) {
+          const double* fsrc = w.f0;
+          if (sub > 0) {
+            g.sync();
+            cell_rates(m, g, a.p, yi, fi, eval_mem(w), (double*)nullptr, false);
+            fsrc = fi;
+          }
+          for (int i = g.t; i < N; i += NT) d[i] = fsrc[i];
+          g.sync();
+          cell_solve(g, w.B, N, w.perm, w.invdiag, d);
+          for (int i = g.t; i < N; i += NT) yi[i] += d[i];
+        }
+        // extrapolation, element by element, and the error of column j
+        double e = 0.0;
+        for (int i = g.t; i < N; i += NT) {
+          double q = yi[i];
+          for (int l = 2; l <= j; ++l) {
+            const double r = (double)j / (double)(j - l + 1);
+            double* tl = tab(l - 1);
+            const double qn = q + (q - tl[i]) / (r - 1.0);
+            tl[i] = q;
+            q = qn;
+          }
+          tab(j)[i] = q;
+          if (j >= 2) {
+            const double sc = a.atol + a.rtol * fmax(fabs(w.y[i]), fabs(q));
+            e = Grp<G>::nanmax(e, fabs(q - tab(j - 1)[i]) / sc);
+          }
+        }
+        g.sync();
+        if (j < 2) continue;
+        e = g.max_nan(e);
+        if (!(e < INFINITY)) { badstep = true; break; }  // NaN or infinite
+        fac_prv = fac_cur;
+        fac_cur = (e > 0.0) ? fmin(4.0, fmax(0.02, 0.94 * pow(e, -1.0 / j))) : 4.0;
+        if (j == k - 1) {
+          if (e <= 1.0) { accepted = j; break; }
+        } else if (j == k) {
+          if (e <= 1.0) { accepted = j; break; }
+          const double ratio = (double)(k + 1);  // n_{k+1} / n_1
+          if (e > ratio * ratio) break;
+        } else if (j == k + 1) {
+          if (e <= 1.0) accepted = j;
+          break;
+        }
+      }
+      if (accepted) {
+        const int c = accepted;
+        t = (H >= a.dt - t) ? a.dt : t + H;
+        const double* tc = tab(c);
+        for (int i = g.t; i < N; i += NT) w.y[i] = tc[i];
+        g.sync();
+        ++nsteps;
+        need_jac = true;
+        // fac_cur = fac_c, fac_prv = fac_{c-1} (c is the last column computed)
+        int knew;
+        double Hn;
+        if (c == 2) {
+          knew = 3;
+          Hn = H * fac_cur * (last_rej ? 1.0 : seulex_work(3) / seulex_work(2));
+        } else if (c <= k) {
+          const double wc = seulex_work(c) / (H * fac_cur), wc1 = seulex_work(c - 1) / (H * fac_prv);
+          knew = c;
+          if (wc1 < 0.8 * wc) knew = c - 1;
+          else if (c == k && wc < 0.9 * wc1) knew = c + 1;
+          Hn = H * (knew < c ? fac_prv : fac_cur) * (knew > c ? seulex_work(knew) / seulex_work(c) : 1.0);
+        } else {
+          const double wc = seulex_work(c) / (H * fac_cur), wc1 = seulex_work(c - 1) / (H * fac_prv);
+          knew = c - 1;
+          if (wc < 0.9 * wc1) knew = c;
+          Hn = H * (knew == c ? fac_cur : fac_prv);
+        }
+        if (last_rej) { Hn = fmin(Hn, H); knew = min(knew, c); }
+        k = max(2, min(knew, kmax - 1));
+        last_rej = false;
+        H_next = Hn;
+        if (t >= a.dt) break;
+      } else {
+        ++nrej;
+        last_rej = true;
+        if (badstep) {
+          H_next = H * 0.2;
+        } else {
+          // gave up at column k (fac_k = fac_cur) or k+1 (fac_k = fac_prv)
+          const int mc = min(k, last);
+          H_next = H * fmin(last == k ? fac_cur : fac_prv, 0.5);
+          k = max(2, mc);
+        }
+      }
+      H = fmin(H_next, a.dt - t);
+    }
+    double ysum = 0.0;
+    for (int i = g.t; i < N; i += NT) {
+      const double v = w.y[i];
+      if (i == 0) a.T[cell] = v;
+      else { a.Y[(size_t)(i - 1) * a.ncells + cell] = v; ysum += v; }
+    }
+    ysum = g.sum(ysum);
+    if (g.t == 0) {
+      if (status != CHEM_CELL_BAD_INPUT) a.Y[(size_t)(K - 1) * a.ncells + cell] = 1.0 - ysum;
+      if (a.h_inout && status != CHEM_CELL_BAD_INPUT) a.h_inout[cell] = H_next;
+      if (a.status) a.status[cell] = status;
+      if (a.steps_out) a.steps_out[cell] = nsteps;
+      if (a.rej_out) a.rej_out[cell] = nrej;
+      atomicAdd(&a.totals[0], (unsigned long long)nsteps);
+      atomicAdd(&a.totals[1], (unsigned long long)nrej);
+      if (status != CHEM_CELL_OK) atomicAdd(&a.totals[2], 1ull);
+    }
+    g.sync();
+  }
+}
+
 // One-shot source term / Jacobian for chem_rates and chem_jacobian.
 template <int G>
 __global__ void __launch_bounds__(256, 1) rates_kernel(DevMech m, Plan plan, double p, const double* T, const double* Y,
@@ -503,7 +700,12 @@ struct Launch {
   Plan plan;
 };
 
-const void* integrate_fn(int G) {
+const void* integrate_fn(int G, int solver) {
+  if (solver == CHEM_SOLVER_SEULEX)
+    return G == 1 ? (const void*)seulex_kernel<1>
+           : G == 2 ? (const void*)seulex_kernel<2>
+           : G == 4 ? (const void*)seulex_kernel<4>
+                    : (const void*)seulex_kernel<8>;
   return G == 1 ? (const void*)integrate_kernel<1>
          : G == 2 ? (const void*)integrate_kernel<2>
          : G == 4 ? (const void*)integrate_kernel<4>
@@ -517,6 +719,15 @@ const void* rates_fn(int G) {
 }
 
 void launch_integrate(const Launch& L, cudaStream_t st, const DevMech& d, const IntegrateArgs& a) {
+  if (a.solver == CHEM_SOLVER_SEULEX) {
+    switch (L.G) {
+      case 1: seulex_kernel<1><<<L.grid, L.threads, L.smem, st>>>(d, L.plan, a); break;
+      case 2: seulex_kernel<2><<<L.grid, L.threads, L.smem, st>>>(d, L.plan, a); break;
+      case 4: seulex_kernel<4><<<L.grid, L.threads, L.smem, st>>>(d, L.plan, a); break;
+      default: seulex_kernel<8><<<L.grid, L.threads, L.smem, st>>>(d, L.plan, a); break;
+    }
+    return;
+  }
   switch (L.G) {
     case 1: integrate_kernel<1><<<L.grid, L.threads, L.smem, st>>>(d, L.plan, a); break;
     case 2: integrate_kernel<2><<<L.grid, L.threads, L.smem, st>>>(d, L.plan, a); break;
@@ -528,7 +739,7 @@ void launch_integrate(const Launch& L, cudaStream_t st, const DevMech& d, const 
 // Launch shape: G warps per cell, as many cells per CTA as the shared memory allows (at most 8
 // warps per CTA, 15 named barriers), one persistent CTA wave.
 int pick_launch(const chem_mech* m, int64_t ncells, int want_G, int want_cpc, int want_ctas_per_sm, bool integ,
-                Launch& L) {
+                Launch& L, int solver = CHEM_SOLVER_ROSENBROCK) {
   int G = want_G;
   if (G <= 0) {
     // automatic: about 8 warps per SM -- G = 8 / (cells that fit), a power of two in 1..8, and
@@ -552,7 +763,7 @@ int pick_launch(const chem_mech* m, int64_t ncells, int want_G, int want_cpc, in
   L.cells_per_cta = cpc;
   L.threads = 32 * G * cpc;
   L.smem = per_cell * cpc;
-  const void* kernel = integ ? integrate_fn(G) : rates_fn(G);
+  const void* kernel = integ ? integrate_fn(G, solver) : rates_fn(G);
   int occ = 0;
   CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, L.threads, L.smem));
@@ -573,7 +784,7 @@ int enqueue_integrate(chem_mech* m, const chem_opts& o, IntegrateArgs a, cudaStr
     a.first = first;
     a.count = std::min(batch, total - first);
     Launch L;
-    int rc = pick_launch(m, a.count, o.warps_per_cell, o.cells_per_cta, o.ctas_per_sm, true, L);
+    int rc = pick_launch(m, a.count, o.warps_per_cell, o.cells_per_cta, o.ctas_per_sm, true, L, a.solver);
     if (rc) return rc;
     CK(cudaMemsetAsync(a.queue, 0, sizeof(int), st));
     launch_integrate(L, st, m->dev, a);
@@ -625,6 +836,7 @@ void chem_default_opts(chem_opts* o) {
   o->warps_per_cell = 0;
   o->use_graph = 0;
   o->batch_cells = 0;
+  o->solver = CHEM_SOLVER_ROSENBROCK;
 }
 
 int chem_load_mechanism(const char* path, chem_mech** out) {
@@ -846,6 +1058,10 @@ static int integrate_impl(const chem_mech* mc, double p_Pa, double* T, double* Y
     return set_err(CHEM_EINVAL, "chem_integrate: unknown precision mode");
   if (o.precision == CHEM_PREC_MIXED && (o.refine_sweeps < 1 || o.refine_sweeps > 4))
     return set_err(CHEM_EINVAL, "chem_integrate: refine_sweeps must be 1..4");
+  if (o.solver != CHEM_SOLVER_ROSENBROCK && o.solver != CHEM_SOLVER_SEULEX)
+    return set_err(CHEM_EINVAL, "chem_integrate: unknown solver");
+  if (o.solver == CHEM_SOLVER_SEULEX && (o.precision != CHEM_PREC_FP64 || rec))
+    return set_err(CHEM_EINVAL, "chem_integrate: Seulex runs in FP64 and without step records");
   if (m->host.K > 128) return set_err(CHEM_ESIZE, "chem_integrate: more than 128 species");
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (ncells == 0) return CHEM_OK;
@@ -878,6 +1094,7 @@ static int integrate_impl(const chem_mech* mc, double p_Pa, double* T, double* Y
   a.ncells = ncells; a.first = 0; a.count = ncells; a.max_steps = o.max_steps; a.use_queue = o.use_queue;
   a.mixed = o.precision == CHEM_PREC_MIXED; a.refine_sweeps = o.refine_sweeps;
   a.rec = rec; a.rec_cap = rec_cap;
+  a.solver = o.solver;
   if (o.use_graph && dev) {
     rc = launch_via_graph(m, o, a, st);
   } else {
@@ -1037,6 +1254,10 @@ int chem_integrate_noalloc(const chem_mech* mc, double p_Pa, double* T, double* 
     return set_err(CHEM_EINVAL, "chem_integrate_noalloc: unknown precision mode");
   if (o.precision == CHEM_PREC_MIXED && (o.refine_sweeps < 1 || o.refine_sweeps > 4))
     return set_err(CHEM_EINVAL, "chem_integrate_noalloc: refine_sweeps must be 1..4");
+  if (o.solver != CHEM_SOLVER_ROSENBROCK && o.solver != CHEM_SOLVER_SEULEX)
+    return set_err(CHEM_EINVAL, "chem_integrate_noalloc: unknown solver");
+  if (o.solver == CHEM_SOLVER_SEULEX && o.precision != CHEM_PREC_FP64)
+    return set_err(CHEM_EINVAL, "chem_integrate_noalloc: Seulex runs in FP64");
   if (m->host.K > 128) return set_err(CHEM_ESIZE, "chem_integrate_noalloc: more than 128 species");
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (ncells == 0) return CHEM_OK;
@@ -1052,7 +1273,7 @@ int chem_integrate_noalloc(const chem_mech* mc, double p_Pa, double* T, double* 
   unsigned char* s = static_cast<unsigned char*>(scratch);
   CK(cudaMemsetAsync(s, 0, kNoAllocCounters, st));  // queue counter and totals start at zero
   Launch L;
-  rc = pick_launch(m, ncells, o.warps_per_cell, o.cells_per_cta, o.ctas_per_sm, true, L);
+  rc = pick_launch(m, ncells, o.warps_per_cell, o.cells_per_cta, o.ctas_per_sm, true, L, o.solver);
   if (rc) return rc;
   int32_t* d_steps = reinterpret_cast<int32_t*>(s + kNoAllocCounters);
   int32_t* d_rej = d_steps + kNoAllocMaxCells;
@@ -1065,6 +1286,7 @@ int chem_integrate_noalloc(const chem_mech* mc, double p_Pa, double* T, double* 
   a.queue = reinterpret_cast<int*>(s);
   a.ncells = ncells; a.first = 0; a.count = ncells; a.max_steps = o.max_steps; a.use_queue = o.use_queue;
   a.mixed = o.precision == CHEM_PREC_MIXED; a.refine_sweeps = o.refine_sweeps;
+  a.solver = o.solver;
   launch_integrate(L, st, m->dev, a);
   CK(cudaGetLastError());
   if (steps) CK(cudaMemcpyAsync(steps, d_steps, sizeof(int32_t) * ncells, cudaMemcpyDeviceToDevice, st));
