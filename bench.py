@@ -72,6 +72,9 @@ def parse_args():
                     help="also time one launch per batch of this many cells (static assignment) against the queue")
     ap.add_argument("--autotune", action="store_true", help="pick warps/cell and cells/CTA with the autotuner first")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--vs-fp64", action="store_true",
+                    help="also run the plain FP64 Rosenbrock path once (untimed result, timed call) and report "
+                         "the speed ratio and the largest deviation of T and Y from it")
     ap.add_argument("--warm-start", action="store_true",
                     help="also time the next CFD step: from the state at dt, with the carried-over sub-step h")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0 = auto)")
@@ -424,6 +427,30 @@ def main():
         "steps_per_cell": {"mean": float(steps_np.mean()), "max": int(steps_np.max()),
                            "rejects_mean": float(rej_np.mean())},
     }
+    if args.vs_fp64:
+        # the plain FP64 Rosenbrock path on the same field, for the comparison the precision and
+        # solver options are judged by (speed at the state the timed path produced)
+        T_ref, Y_ref = T_out.clone(), Y_out.clone()
+        fopts = chem.default_opts(precision=chem.CHEM_PREC_FP64, solver=chem.CHEM_SOLVER_ROSENBROCK)
+        fopts.use_graph = 1
+        T.copy_(T_host)
+        Y.copy_(Y_host)
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        chem.chem_integrate(mech, w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], status=status, opts=fopts)
+        e1.record(stream)
+        e1.synchronize()
+        fms = e0.elapsed_time(e1)
+        Tf, Yf = T.cpu().numpy(), Y.cpu().numpy()
+        dT = np.abs(T_ref.numpy() - Tf) / np.abs(Tf)
+        dY = np.abs(Y_ref.numpy() - Yf)
+        line["vs_fp64"] = {"fp64_ms_per_step": fms, "speedup": fms / (kern_ms / args.steps),
+                           "max_rel_err_T": float(dT.max()),
+                           "max_abs_err_Y": float(dY.max()),
+                           "max_err_Y_in_tol_units": float((dY / (w["atol"] + w["rtol"] * np.abs(Yf))).max()),
+                           "max_err_T_in_tol_units": float((np.abs(T_ref.numpy() - Tf) /
+                                                            (w["atol"] + w["rtol"] * np.abs(Tf))).max())}
     if args.warm_start:
         # the next CFD step of the same field: an untimed cold call leaves T, Y at dt and the
         # controller's proposal in h; the timed call continues from there (Sec. 2.3: the previous
