@@ -75,6 +75,12 @@ struct IntegrateArgs {
 // ------------------------------------------------------------------------------------------
 // Mixed precision (FP32 LU + FP64-residual iterative refinement).
 
+// After an attempt whose FP32 refinement did not converge, the cell's next attempts use FP64
+// factors directly (the iteration matrix changes slowly from step to step)
+#ifndef CHEM_MIXED_FP64_RUN
+#define CHEM_MIXED_FP64_RUN 16
+#endif
+
 // Equilibrate W = I gh - J by powers of two (row exponents er, then column exponents ec, from
 // the largest entries) and factor S = D_r W D_c in FP32 in the first half of buffer B.
 template <int G>
@@ -278,7 +284,7 @@ __global__ void __launch_bounds__(256, 1) integrate_kernel(DevMech m, Plan plan,
         }
         if (!conv) {
           if (g.t == 0) atomicAdd(&a.totals[3], 1ull);
-          f64_until = attempt + 16;
+          f64_until = attempt + CHEM_MIXED_FP64_RUN;
           continue;  // redo this attempt with FP64 factors
         }
         // solution, embedded error, filtered through (I - gamma h J)^-1 = W^-1 / (gamma h)
