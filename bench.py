@@ -65,7 +65,7 @@ def parse_args():
                     help="integrator: the 4-stage Rosenbrock method or the paper's Seulex")
     ap.add_argument("--cells", type=int, default=0, help="cells per rank (0 = the full 65536-cell field)")
     ap.add_argument("--dt", type=float, default=0.0, help="override the CFD time step (profiling small cases)")
-    ap.add_argument("--workload", choices=["shear", "uneven", "adjoint"], default="shear",
+    ap.add_argument("--workload", choices=["shear", "uneven", "adjoint", "0d"], default="shear",
                     help="shear: 53-species shear layer (the headline); uneven: 100-species igniting/cold/burnt field")
     ap.add_argument("--order", choices=["shuffled", "blocked"], default="blocked", help="cell order of --workload uneven")
     ap.add_argument("--batch-cells", type=int, default=0,
@@ -314,12 +314,91 @@ def run_adjoint(args, world, rank, local):
     return 0
 
 
+def run_ablation(args, world, rank, local):
+    """The paper's Fig. 3 experiment on the GPU (Sec. 2.3): a 0D reactor (the 53-species mechanism
+    at 1200 K, 13.5 atm) advanced over CFD steps of 1e-6 s with the step carried over, timed for
+    each absolute tolerance with (forward-difference Jacobian, FP64 LU), (analytical Jacobian, FP64
+    LU), (analytical Jacobian, FP32 LU + FP64 refinement) and Seulex."""
+    import torch
+    from paper_2105_12070_gb300 import chem, ranks, synth
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n = args.cells or 608
+    w = synth.workload_0d(n)
+    mech = chem.Mechanism(w["mech"].write_temp())
+    ncfd = 50
+    variants = [("fd_fp64", dict(jacobian=chem.CHEM_JAC_FD)),
+                ("analytic_fp64", dict()),
+                ("analytic_mixed", dict(precision=chem.CHEM_PREC_MIXED)),
+                ("seulex", dict(solver=chem.CHEM_SOLVER_SEULEX))]
+    atols = (1e-8, 1e-10, 1e-12, 1e-14)
+    T = torch.empty(n, dtype=torch.float64, device="cuda")
+    Y = torch.empty((mech.K, n), dtype=torch.float64, device="cuda")
+    h = torch.zeros(n, dtype=torch.float64, device="cuda")
+    status = torch.zeros(n, dtype=torch.int32, device="cuda")
+    T0 = torch.from_numpy(w["T"]).cuda()
+    Y0 = torch.from_numpy(w["Y"]).cuda()
+    stream = torch.cuda.current_stream()
+    rows = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    for name, kw in variants:
+        opts = chem.default_opts(**kw)
+        for atol in atols:
+            for rep in range(2):  # the first pass warms the launch path, the second is timed
+                T.copy_(T0)
+                Y.copy_(Y0)
+                h.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                steps = 0
+                for _ in range(ncfd):
+                    st = chem.chem_integrate(mech, w["p_Pa"], T, Y, w["dt"], w["rtol"], atol, h_inout=h,
+                                             status=status, opts=opts, want_stats=True)
+                    steps += st.steps
+                e1.record(stream)
+                e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            rows.append({"variant": name, "atol": atol, "ms": ms, "ms_per_cfd_step": ms / ncfd,
+                         "steps_per_cell": steps / n, "T_final": float(T[0].item()),
+                         "failed_cells": int((status != 0).sum().item())})
+    clk = clocks.stop()
+    ms_all = ranks.max_over_ranks([r["ms"] for r in rows], device="cuda")
+    for r, m in zip(rows, ms_all):
+        r["ms"] = m
+    ref = {r["atol"]: r["ms"] for r in rows if r["variant"] == "analytic_fp64"}
+    for r in rows:
+        r["time_vs_analytic_fp64"] = r["ms"] / ref[r["atol"]]
+    head = next(r for r in rows if r["variant"] == "analytic_fp64" and r["atol"] == 1e-10)
+    line = {
+        "metric": "0D reactor: time per CFD step vs absolute tolerance (Fig. 3 analogue)",
+        "value": head["ms_per_cfd_step"], "unit": "ms per CFD step (608 reactors)", "n_gpus": world,
+        "steps": ncfd, "warmup": 1, "ms_per_step": head["ms_per_cfd_step"], "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "cells": n, "species": mech.K, "reactions": mech.R, "dt_s": w["dt"],
+                   "p_atm": 13.5, "T0_K": 1200.0, "rtol": w["rtol"], "cfd_steps": ncfd},
+        "ablation": rows, "clocks": clk, "gpu_launches": None, "roofline": None,
+        "e2e": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
     from paper_2105_12070_gb300 import synth
     if args.workload == "adjoint" and args.impl == "gpu":
         return run_adjoint(args, world, rank, local)
+    if args.workload == "0d" and args.impl == "gpu":
+        return run_ablation(args, world, rank, local)
     if args.workload == "uneven":
         w = synth.workload_uneven(args.cells or 262144, args.order)
     else:

@@ -54,6 +54,11 @@ extern "C" {
                                     extrapolation, harmonic step-number sequence, up to 8 columns,
                                     order and step chosen by work per unit step; FP64 only */
 
+/* Jacobian of the Rosenbrock solve (chem_opts.jacobian) */
+#define CHEM_JAC_ANALYTIC 0 /* the analytical Jacobian (Sec. 2.3; default) */
+#define CHEM_JAC_FD 1       /* first-order forward differences, N + 1 rate evaluations: the
+                               alternative the paper measures the analytical Jacobian against */
+
 #define CHEM_PREC_FP64 0   /* FP64 LU and substitutions */
 #define CHEM_PREC_MIXED 1  /* FP32 LU + FP64-residual iterative refinement; rates, Kc, error
                               norm, step control and state update stay FP64 */
@@ -76,6 +81,7 @@ typedef struct {
                          kernel launch per batch (the one-launch-per-batch comparison of the
                          persistent queue); 0 (default): one launch for all cells */
   int solver;         /* CHEM_SOLVER_ROSENBROCK (default) or CHEM_SOLVER_SEULEX */
+  int jacobian;       /* CHEM_JAC_ANALYTIC (default) or CHEM_JAC_FD (Rosenbrock only) */
 } chem_opts;
 
 typedef struct {

@@ -76,6 +76,7 @@ def _load():
                                                     ctypes.c_double, ctypes.c_double, _dp, ctypes.c_int, _ip]
             lib.oracle_replay.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, ctypes.c_int, _dp, _dp, _dp,
                                           _dp, _dp]
+            lib.oracle_jacobian_fd.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp]
             lib.oracle_jacobian_dir.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
             _lib = lib
     return _lib
@@ -152,8 +153,9 @@ class OracleMechanism:
     def integrate(self, p_Pa: float, T, Y, dt: float, rtol: float = 1e-6, atol: float = 1e-10, h_inout=None,
                   max_steps: int = 100000, nthreads: int = 1, solver: str = "rosenbrock"):
         """Returns (T, Y, status, steps, rejects); inputs are not modified; h_inout is updated in place.
-        solver: "rosenbrock" (the 4-stage method) or "seulex" (extrapolated linearly implicit Euler)."""
-        solver_id = {"rosenbrock": 0, "seulex": 1}[solver]
+        solver: "rosenbrock" (the 4-stage method), "seulex" (extrapolated linearly implicit Euler) or
+        "rosenbrock_fdjac" (the 4-stage method with the forward-difference Jacobian)."""
+        solver_id = {"rosenbrock": 0, "seulex": 1, "rosenbrock_fdjac": 2}[solver]
         T = _f64(T).copy()
         Y = _f64(Y).copy()
         n = T.shape[0]
@@ -192,6 +194,13 @@ class OracleMechanism:
         if rc != 0:
             raise RuntimeError("oracle replay hit a singular iteration matrix")
         return (out, dout) if dout is not None else out
+
+    def jacobian_fd(self, p_Pa: float, phi):
+        """Forward-difference Jacobian at one state phi = [T, Y_1..Y_{K-1}]."""
+        phi = _f64(phi)
+        J = np.zeros((self.N, self.N))
+        self._lib.oracle_jacobian_fd(self._h, float(p_Pa), _p(phi), _p(J))
+        return J
 
     def jacobian_dir(self, p_Pa: float, phi, dphi=None, dlnA=None):
         """At one state phi: (f, J, df, dJ), df and dJ the derivatives of f and J along

@@ -487,6 +487,28 @@ static void jacobian(const Mech& m, double p, const S* phi, S* f, S* J, const S*
 }
 
 // ----------------------------------------------------------------------------------------------
+// First-order forward-difference Jacobian: the alternative the paper measures the analytical
+// Jacobian against (Sec. 2.3; "first-order finite differencing", N + 1 rate evaluations).
+// Column j = (f(phi + d_j e_j) - f(phi)) / d_j, d_j = 2^-26 max(|phi_j|, s_j), s_0 = 1 K for T and
+// s_j = 1e-6 for the mass fractions; f0 = f(phi) on return.
+
+static void jacobian_fd(const Mech& m, double p, const double* phi, double* f0, double* J) {
+  const int N = m.K;
+  RateState<double> st;
+  rates(m, p, phi, f0, st);
+  std::vector<double> x(phi, phi + N), fj(N);
+  for (int j = 0; j < N; ++j) {
+    const double d = 0x1p-26 * std::max(std::fabs(phi[j]), j == 0 ? 1.0 : 1e-6);
+    x[j] = phi[j] + d;
+    const double dj = x[j] - phi[j];  // the step actually taken
+    RateState<double> sj;
+    rates(m, p, x.data(), fj.data(), sj);
+    for (int i = 0; i < N; ++i) J[(size_t)i * N + j] = (fj[i] - f0[i]) / dj;
+    x[j] = phi[j];
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
 // Dense LU with partial pivoting (textbook Doolittle, row interchanges; ties go to the lowest
 // row index) and the forward / back substitution that uses it.
 
@@ -562,7 +584,8 @@ struct CellStats {
 // 0.2.  The last step is clipped so that t reaches dt exactly.  The cold-start step is
 // 0.01 dt; a positive h_inout overrides it (carry-over of the chemistry sub-step, Sec. 2.3).
 static int integrate_cell(const Mech& m, double p, double* phi, double dt, double rtol, double atol, double* h_io,
-                          int max_steps, CellStats& cs, std::vector<double>* h_record = nullptr) {
+                          int max_steps, CellStats& cs, std::vector<double>* h_record = nullptr,
+                          bool fd_jacobian = false) {
   const int N = m.K;
   if (!(std::isfinite(phi[0]) && phi[0] > 0.0)) return kBadInput;
   for (int i = 1; i < N; ++i)
@@ -581,8 +604,13 @@ static int integrate_cell(const Mech& m, double p, double* phi, double dt, doubl
     if (attempt >= max_steps) { status = kMaxSteps; break; }
     if (h_next_unclipped < 1e-14 * dt) { status = kHUnderflow; break; }
     if (need_jac) {
-      jacobian(m, p, y.data(), f0.data(), J.data());
-      cs.f_evals++;
+      if (fd_jacobian) {
+        jacobian_fd(m, p, y.data(), f0.data(), J.data());
+        cs.f_evals += N + 1;
+      } else {
+        jacobian(m, p, y.data(), f0.data(), J.data());
+        cs.f_evals++;
+      }
       need_jac = false;
     }
     for (size_t e = 0; e < (size_t)N * N; ++e) A[e] = -c.gamma * h * J[e];
@@ -978,6 +1006,14 @@ int oracle_jacobian_dir(void* h, double p_Pa, const double* phi, const double* d
   return 0;
 }
 
+// Forward-difference Jacobian of f at one state phi (N): J[N][N] (row i = d f_i / d phi).
+int oracle_jacobian_fd(void* h, double p_Pa, const double* phi, double* J) {
+  Mech* m = static_cast<Mech*>(h);
+  std::vector<double> f0(m->K);
+  jacobian_fd(*m, p_Pa * 10.0, phi, f0.data(), J);
+  return 0;
+}
+
 // Complex-step Jacobian of f at one state: Jcs[N][N] with Jcs[i][j] = Im f_i(phi + i h e_j)/h.
 int oracle_jacobian_cs(void* h, double p_Pa, double T, const double* Y, double step, double* Jcs) {
   Mech* m = static_cast<Mech*>(h);
@@ -997,7 +1033,8 @@ int oracle_jacobian_cs(void* h, double p_Pa, double T, const double* Y, double s
 
 // Integrate n cells over dt.  T[n] and Y[K][n] are updated in place (Y_K = 1 - sum of the
 // others on output).  h_inout[n] may be NULL.  status[n], steps[n], rejects[n] may be NULL.
-// solver 0 = Rosenbrock (integrate_cell), 1 = Seulex (integrate_cell_seulex).
+// solver 0 = Rosenbrock (integrate_cell), 1 = Seulex (integrate_cell_seulex), 2 = Rosenbrock
+// with the forward-difference Jacobian.
 int oracle_integrate(void* h, double p_Pa, int64_t n, double* T, double* Y, double dt, double rtol, double atol,
                      double* h_inout, int32_t* status, int32_t* steps, int32_t* rejects, int max_steps, int nthreads,
                      int solver) {
@@ -1017,7 +1054,7 @@ int oracle_integrate(void* h, double p_Pa, int64_t n, double* T, double* Y, doub
                    ? integrate_cell_seulex(*m, p_Pa * 10.0, phi.data(), dt, rtol, atol,
                                            h_inout ? &h_inout[c] : nullptr, max_steps, cs)
                    : integrate_cell(*m, p_Pa * 10.0, phi.data(), dt, rtol, atol, h_inout ? &h_inout[c] : nullptr,
-                                    max_steps, cs);
+                                    max_steps, cs, nullptr, solver == 2);
       T[c] = phi[0];
       double ysum = 0.0;
       for (int k = 0; k < K - 1; ++k) { Y[(size_t)k * n + c] = phi[1 + k]; ysum += phi[1 + k]; }

@@ -20,6 +20,8 @@ _lib = None
 
 CHEM_SOLVER_ROSENBROCK = 0
 CHEM_SOLVER_SEULEX = 1
+CHEM_JAC_ANALYTIC = 0
+CHEM_JAC_FD = 1
 CHEM_PREC_FP64 = 0
 CHEM_PREC_MIXED = 1
 CELL_STATUS = {0: "ok", 1: "max_steps", 2: "h_underflow", 3: "bad_input", 4: "record_full"}
@@ -30,7 +32,7 @@ class ChemOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("refine_sweeps", ctypes.c_int), ("max_steps", ctypes.c_int),
                 ("use_queue", ctypes.c_int), ("cells_per_cta", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("warps_per_cell", ctypes.c_int), ("use_graph", ctypes.c_int), ("batch_cells", ctypes.c_int),
-                ("solver", ctypes.c_int)]
+                ("solver", ctypes.c_int), ("jacobian", ctypes.c_int)]
 
 
 class ChemStats(ctypes.Structure):

@@ -70,7 +70,29 @@ struct IntegrateArgs {
   double* rec;        // record mode: checkpoint of every accepted step (NULL: off)
   int rec_cap;        // checkpoints per cell
   int solver;         // CHEM_SOLVER_*
+  int fdjac;          // forward-difference Jacobian instead of the analytical one
 };
+
+// First-order forward-difference Jacobian (the alternative the paper measures the analytical
+// Jacobian against, Sec. 2.3): N + 1 rate evaluations.  Column j = (f(y + d_j e_j) - f(y)) / d_j,
+// d_j = 2^-26 max(|y_j|, s_j), s = 1 K for T and 1e-6 for the mass fractions (d_j taken as the
+// step actually represented).  Leaves f(y) in w.f0 and -J in w.A (the analytical path's layout).
+template <int G>
+__device__ void cell_fd_jacobian(const DevMech& m, const Grp<G>& g, double p, const CellMem& w) {
+  constexpr int NT = Grp<G>::NT;
+  const int N = m.N;
+  cell_rates(m, g, p, w.y, w.f0, eval_mem(w), (double*)nullptr, false);
+  for (int j = 0; j < N; ++j) {
+    const double yj = w.y[j];
+    const double xj = yj + 0x1p-26 * fmax(fabs(yj), j == 0 ? 1.0 : 1e-6);
+    const double dj = xj - yj;
+    for (int i = g.t; i < N; i += NT) w.ynew[i] = (i == j) ? xj : w.y[i];
+    g.sync();
+    cell_rates(m, g, p, w.ynew, w.fs, eval_mem(w), (double*)nullptr, false);
+    for (int i = g.t; i < N; i += NT) w.A[i * N + j] = -((w.fs[i] - w.f0[i]) / dj);
+    g.sync();
+  }
+}
 
 // ------------------------------------------------------------------------------------------
 // Mixed precision (FP32 LU + FP64-residual iterative refinement).
@@ -220,9 +242,13 @@ __global__ void __launch_bounds__(256, 1) integrate_kernel(DevMech m, Plan plan,
       if (h_next < 1e-14 * a.dt) { status = CHEM_CELL_H_UNDERFLOW; break; }
       PHASE_BEGIN
       if (need_jac) {
-        const CellScalars s0 = cell_rates(m, g, a.p, w.y, w.f0, eval_mem(w), w.A, true);
-        PHASE_END(0);
-        cell_jacobian(m, g, s0, w.f0, eval_mem(w), w.A, w.B);
+        if (a.fdjac) {
+          cell_fd_jacobian(m, g, a.p, w);
+        } else {
+          const CellScalars s0 = cell_rates(m, g, a.p, w.y, w.f0, eval_mem(w), w.A, true);
+          PHASE_END(0);
+          cell_jacobian(m, g, s0, w.f0, eval_mem(w), w.A, w.B);
+        }
         PHASE_END(1);
         need_jac = false;
       }
@@ -843,6 +869,7 @@ void chem_default_opts(chem_opts* o) {
   o->use_graph = 0;
   o->batch_cells = 0;
   o->solver = CHEM_SOLVER_ROSENBROCK;
+  o->jacobian = CHEM_JAC_ANALYTIC;
 }
 
 int chem_load_mechanism(const char* path, chem_mech** out) {
@@ -1068,6 +1095,11 @@ static int integrate_impl(const chem_mech* mc, double p_Pa, double* T, double* Y
     return set_err(CHEM_EINVAL, "chem_integrate: unknown solver");
   if (o.solver == CHEM_SOLVER_SEULEX && (o.precision != CHEM_PREC_FP64 || rec))
     return set_err(CHEM_EINVAL, "chem_integrate: Seulex runs in FP64 and without step records");
+  if (o.jacobian != CHEM_JAC_ANALYTIC && o.jacobian != CHEM_JAC_FD)
+    return set_err(CHEM_EINVAL, "chem_integrate: unknown Jacobian mode");
+  if (o.jacobian == CHEM_JAC_FD && (o.solver != CHEM_SOLVER_ROSENBROCK || rec))
+    return set_err(CHEM_EINVAL, "chem_integrate: the finite-difference Jacobian serves the Rosenbrock solve only, "
+                                "without step records");
   if (m->host.K > 128) return set_err(CHEM_ESIZE, "chem_integrate: more than 128 species");
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (ncells == 0) return CHEM_OK;
@@ -1101,6 +1133,7 @@ static int integrate_impl(const chem_mech* mc, double p_Pa, double* T, double* Y
   a.mixed = o.precision == CHEM_PREC_MIXED; a.refine_sweeps = o.refine_sweeps;
   a.rec = rec; a.rec_cap = rec_cap;
   a.solver = o.solver;
+  a.fdjac = o.jacobian == CHEM_JAC_FD;
   if (o.use_graph && dev) {
     rc = launch_via_graph(m, o, a, st);
   } else {
@@ -1264,6 +1297,8 @@ int chem_integrate_noalloc(const chem_mech* mc, double p_Pa, double* T, double* 
     return set_err(CHEM_EINVAL, "chem_integrate_noalloc: unknown solver");
   if (o.solver == CHEM_SOLVER_SEULEX && o.precision != CHEM_PREC_FP64)
     return set_err(CHEM_EINVAL, "chem_integrate_noalloc: Seulex runs in FP64");
+  if (o.jacobian != CHEM_JAC_ANALYTIC && (o.jacobian != CHEM_JAC_FD || o.solver != CHEM_SOLVER_ROSENBROCK))
+    return set_err(CHEM_EINVAL, "chem_integrate_noalloc: bad Jacobian mode");
   if (m->host.K > 128) return set_err(CHEM_ESIZE, "chem_integrate_noalloc: more than 128 species");
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (ncells == 0) return CHEM_OK;
@@ -1293,6 +1328,7 @@ int chem_integrate_noalloc(const chem_mech* mc, double p_Pa, double* T, double* 
   a.ncells = ncells; a.first = 0; a.count = ncells; a.max_steps = o.max_steps; a.use_queue = o.use_queue;
   a.mixed = o.precision == CHEM_PREC_MIXED; a.refine_sweeps = o.refine_sweeps;
   a.solver = o.solver;
+  a.fdjac = o.jacobian == CHEM_JAC_FD;
   launch_integrate(L, st, m->dev, a);
   CK(cudaGetLastError());
   if (steps) CK(cudaMemcpyAsync(steps, d_steps, sizeof(int32_t) * ncells, cudaMemcpyDeviceToDevice, st));

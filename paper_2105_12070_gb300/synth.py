@@ -378,6 +378,19 @@ def workload_shear_layer(n_side: int = 256):
                 rtol=1e-6, atol=1e-10)
 
 
+def workload_0d(n: int = 608):
+    """The 0D homogeneous-reactor stand-in of the paper's Fig. 2/3 ablation: the 53-species
+    mechanism at 1200 K and 13.5 atm, one Dirichlet(1) mixture (seed 106) in n identical cells
+    (repeated samples of one reactor), CFD step 1e-6 s."""
+    mech = mechanism_53()
+    rng = np.random.default_rng(106)
+    Y1 = rng.dirichlet(np.ones(mech.K))
+    T = np.full(n, 1200.0)
+    Y = np.repeat(Y1[:, None], n, axis=1).copy()
+    return dict(name=f"mech53_0d_reactor{n}", mech=mech, p_Pa=13.5 * P_ATM_PA, T=T, Y=Y, dt=1e-6, rtol=1e-6,
+                atol=1e-10)
+
+
 def workload_igniting(n: int = 16384):
     """53 species, igniting band T ~ U[1000, 1300] K, Dirichlet(1) Y, 20 atm, dt 1e-4 s."""
     mech = mechanism_53()
