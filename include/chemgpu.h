@@ -148,6 +148,24 @@ int chem_integrate_noalloc(const chem_mech* mech, double p_Pa, double* T, double
                            double rtol, double atol, double* h_inout, int32_t* status, int32_t* steps,
                            int32_t* rejects, const chem_opts* opts, chem_stats* stats, void* stream);
 
+/* chem_integrate with zonal reference-cell mapping (DLBFoam's, Sec. 2.2): a cell whose state
+ * lies within |T - T_r| <= tol_T and max_k |Y_k - Y_r,k| <= tol_Y of reference state r (an ambient
+ * zone of low reactivity; the first such r) is not solved: it receives that reference's change
+ * over dt, T += T_r(dt) - T_r, Y_k += Y_r,k(dt) - Y_r,k (k < K-1), Y_K = 1 - sum, and the
+ * reference's status.  The other cells and the references are solved together by chem_integrate
+ * (references from a cold start; a solved cell keeps its h_inout carry-over, a mapped cell's is
+ * left unchanged).
+ *   refs[n_ref][1 + K] (HOST array, n_ref <= 64): T_r, Y_r,0 .. Y_r,K-1;
+ *   zone[ncells] (device, may be NULL): the reference a cell was mapped to, or -1 if solved;
+ *   *n_mapped (host, may be NULL): the number of mapped cells.
+ * The other arrays are device arrays as for chem_integrate.  The call synchronises `stream` once
+ * (after classifying, to size the solve); opts->use_graph is ignored.  The paper has no
+ * formulas for the mapping; the zone test is this library's reading of it. */
+int chem_integrate_mapped(const chem_mech* mech, double p_Pa, double* T, double* Y, int64_t ncells, double dt,
+                          double rtol, double atol, double* h_inout, int32_t* status, const double* refs,
+                          int32_t n_ref, double tol_T, double tol_Y, int32_t* zone, int64_t* n_mapped,
+                          const chem_opts* opts, chem_stats* stats, void* stream);
+
 /* Sensitivities (the discrete adjoint of the integrator).  The paper integrates forward only;
  * these entry points differentiate its solve: the map (phi_0, ln A) -> phi(dt) computed by the
  * accepted Rosenbrock steps of Sec. 2.3 (Eq. 2), with the step sizes frozen at the values the

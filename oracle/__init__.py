@@ -169,6 +169,37 @@ class OracleMechanism:
                                    int(nthreads), solver_id)
         return T, Y, status, steps, rej
 
+    def integrate_mapped(self, p_Pa: float, T, Y, dt: float, refs, tol_T: float, tol_Y: float, rtol: float = 1e-6,
+                         atol: float = 1e-10, nthreads: int = 1):
+        """Zonal reference-cell mapping (DLBFoam's, Sec. 2.2) on top of integrate: a cell within
+        |T - T_r| <= tol_T and max_k |Y_k - Y_r,k| <= tol_Y of reference r (the first such) is not
+        solved; it takes the reference's change over dt (T and Y_0..Y_{K-2}; Y_{K-1} = 1 - sum).
+        refs: (n_ref, 1 + K).  Returns (T, Y, status, zone)."""
+        T = _f64(T)
+        Y = _f64(Y)
+        refs = np.atleast_2d(_f64(refs))
+        n = T.shape[0]
+        zone = np.full(n, -1, np.int32)
+        for c in range(n):
+            for r in range(refs.shape[0]):
+                if abs(T[c] - refs[r, 0]) <= tol_T and np.all(np.abs(Y[:, c] - refs[r, 1:]) <= tol_Y):
+                    zone[c] = r
+                    break
+        solve = np.nonzero(zone < 0)[0]
+        Ts = np.concatenate([T[solve], refs[:, 0]])
+        Ys = np.concatenate([Y[:, solve], refs[:, 1:].T], axis=1)
+        To, Yo, st, _, _ = self.integrate(p_Pa, Ts, Ys, dt, rtol, atol, nthreads=nthreads)
+        Tn, Yn, status = T.copy(), Y.copy(), np.zeros(n, np.int32)
+        Tn[solve], Yn[:, solve], status[solve] = To[:solve.size], Yo[:, :solve.size], st[:solve.size]
+        for c in np.nonzero(zone >= 0)[0]:
+            r = zone[c]
+            i = solve.size + r
+            Tn[c] = T[c] + (To[i] - refs[r, 0])
+            Yn[:-1, c] = Y[:-1, c] + (Yo[:-1, i] - refs[r, 1:-1])
+            Yn[-1, c] = 1.0 - Yn[:-1, c].sum()
+            status[c] = st[i]
+        return Tn, Yn, status, zone
+
     def integrate_record(self, p_Pa: float, phi, dt: float, rtol: float = 1e-6, atol: float = 1e-10,
                          max_hs: int = 100000):
         """One cell, phi = [T, Y_1..Y_{K-1}]: returns (phi_final, accepted step sizes, status)."""

@@ -78,11 +78,15 @@ def load_library(build_if_missing: bool = True):
         lib.chem_integrate_record.argtypes = [vp, dp, vp, vp, i64, dp, dp, dp, vp, vp, vp, ctypes.c_int32, vp,
                                               ctypes.POINTER(ChemOpts), ctypes.POINTER(ChemStats), vp]
         lib.chem_adjoint.argtypes = [vp, dp, i64, vp, ctypes.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.chem_integrate_mapped.argtypes = [vp, dp, vp, vp, i64, dp, dp, dp, vp, vp, vp, ctypes.c_int32, dp, dp,
+                                              vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ChemOpts),
+                                              ctypes.POINTER(ChemStats), vp]
         lib.chem_get_lnA.argtypes = [vp, vp]
         lib.chem_set_lnA.argtypes = [vp, vp]
         for name in ("chem_load_mechanism", "chem_mech_dims", "chem_rates", "chem_jacobian", "chem_integrate",
                      "chem_last_cell_counters", "chem_probe_fp64_peak", "chem_integrate_noalloc",
-                     "chem_debug_exp", "chem_integrate_record", "chem_adjoint", "chem_get_lnA", "chem_set_lnA"):
+                     "chem_debug_exp", "chem_integrate_record", "chem_adjoint", "chem_get_lnA", "chem_set_lnA",
+                     "chem_integrate_mapped"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -276,6 +280,31 @@ def chem_adjoint(mech: Mechanism, p_Pa: float, rec, nsteps, status, gT, gY, gT0,
     pgC, _ = _ptr(g_lnA_cells, np.float64)
     _check(mech._lib.chem_adjoint(mech.handle, float(p_Pa), n, ptrs[0], int(rec.shape[1]), pn, ps, pgT, pgY, pgT0,
                                   pgY0, pgA, pgC, _stream(stream, dev)))
+
+
+def chem_integrate_mapped(mech: Mechanism, p_Pa: float, T, Y, dt: float, refs, tol_T: float, tol_Y: float,
+                          rtol: float = 1e-6, atol: float = 1e-10, h_inout=None, status=None, zone=None,
+                          opts: ChemOpts | None = None, want_stats: bool = False, stream=None):
+    """chem_integrate with zonal reference-cell mapping: refs is a host array (n_ref, 1 + K) of
+    reference states [T, Y_0..Y_{K-1}]; cells within (tol_T, tol_Y) of a reference take its change
+    over dt instead of being solved.  Device tensors otherwise.  Returns (n_mapped, ChemStats or None)."""
+    n = _cells(mech, T, Y)
+    r = np.ascontiguousarray(np.asarray(refs, dtype=np.float64))
+    if r.ndim != 2 or r.shape[1] != mech.K + 1:
+        raise ValueError(f"refs must have shape (n_ref, K+1={mech.K + 1})")
+    pT, dT = _ptr(T, np.float64)
+    pY, _ = _ptr(Y, np.float64)
+    ph, _ = _ptr(h_inout, np.float64)
+    ps, _ = _ptr(status, np.int32)
+    pz, _ = _ptr(zone, np.int32)
+    nm = ctypes.c_int64()
+    st = ChemStats() if want_stats else None
+    _check(mech._lib.chem_integrate_mapped(mech.handle, float(p_Pa), pT, pY, n, float(dt), float(rtol), float(atol),
+                                           ph, ps, ctypes.c_void_p(r.ctypes.data), int(r.shape[0]), float(tol_T),
+                                           float(tol_Y), pz, ctypes.byref(nm),
+                                           ctypes.byref(opts) if opts is not None else None,
+                                           ctypes.byref(st) if st is not None else None, _stream(stream, dT)))
+    return nm.value, st
 
 
 def chem_get_lnA(mech: Mechanism) -> np.ndarray:

@@ -628,6 +628,84 @@ __global__ void __launch_bounds__(256) fp64_peak_kernel(double* out, int iters, 
 }
 
 // ------------------------------------------------------------------------------------------
+// Zonal reference-cell mapping (DLBFoam's, Sec. 2.2): cells whose state lies within a tolerance
+// of a reference state (an ambient zone of low reactivity) are not solved; they receive the
+// reference state's change over dt.  Three small kernels around the ordinary solve: classify
+// (and compact the cells to solve), gather (the compact state, plus the references appended),
+// scatter (solved cells back, mapped cells shifted by their reference's change).
+
+// refs: [n_ref][1 + K] = T, Y_0 .. Y_{K-1}.  zone[c] = first reference within |T - T_r| <= tol_T
+// and max_k |Y_k - Y_r,k| <= tol_Y, or -1; cells with zone -1 get a compact position pos[c].
+__global__ void map_classify_kernel(const double* T, const double* Y, int64_t ncells, int K, const double* refs,
+                                    int n_ref, double tol_T, double tol_Y, int32_t* zone, int64_t* pos,
+                                    int64_t* list, unsigned long long* count) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  int z = -1;
+  for (int r = 0; r < n_ref && z < 0; ++r) {
+    const double* rf = refs + (size_t)r * (1 + K);
+    bool ok = fabs(T[c] - rf[0]) <= tol_T;
+    for (int k = 0; ok && k < K; ++k) ok = fabs(Y[(size_t)k * ncells + c] - rf[1 + k]) <= tol_Y;
+    if (ok) z = r;
+  }
+  zone[c] = z;
+  if (z < 0) {
+    const int64_t i = (int64_t)atomicAdd(count, 1ull);
+    pos[c] = i;
+    list[i] = c;
+  }
+}
+
+// compact state: the n_un cells to solve, then the n_ref references (cold start)
+__global__ void map_gather_kernel(const double* T, const double* Y, const double* h, int64_t ncells, int K,
+                                  const double* refs, int n_ref, const int64_t* list, int64_t n_un, double* Tc,
+                                  double* Yc, double* hc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nc = n_un + n_ref;
+  if (i >= nc) return;
+  if (i < n_un) {
+    const int64_t c = list[i];
+    Tc[i] = T[c];
+    for (int k = 0; k < K; ++k) Yc[(size_t)k * nc + i] = Y[(size_t)k * ncells + c];
+    hc[i] = h ? h[c] : 0.0;
+  } else {
+    const double* rf = refs + (size_t)(i - n_un) * (1 + K);
+    Tc[i] = rf[0];
+    for (int k = 0; k < K; ++k) Yc[(size_t)k * nc + i] = rf[1 + k];
+    hc[i] = 0.0;
+  }
+}
+
+__global__ void map_scatter_kernel(double* T, double* Y, double* h, int32_t* status, int64_t ncells, int K,
+                                   const double* refs, const int32_t* zone, const int64_t* pos, int64_t n_un,
+                                   int n_ref, const double* Tc, const double* Yc, const double* hc,
+                                   const int32_t* sc) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  const int64_t nc = n_un + n_ref;
+  const int z = zone[c];
+  if (z < 0) {
+    const int64_t i = pos[c];
+    T[c] = Tc[i];
+    for (int k = 0; k < K; ++k) Y[(size_t)k * ncells + c] = Yc[(size_t)k * nc + i];
+    if (h) h[c] = hc[i];
+    if (status) status[c] = sc[i];
+  } else {
+    const int64_t i = n_un + z;
+    const double* rf = refs + (size_t)z * (1 + K);
+    T[c] += Tc[i] - rf[0];
+    double ysum = 0.0;
+    for (int k = 0; k < K - 1; ++k) {
+      const double v = Y[(size_t)k * ncells + c] + (Yc[(size_t)k * nc + i] - rf[1 + k]);
+      Y[(size_t)k * ncells + c] = v;
+      ysum += v;
+    }
+    Y[(size_t)(K - 1) * ncells + c] = 1.0 - ysum;
+    if (status) status[c] = sc[i];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // Scratch of chem_integrate_noalloc: a fixed device array instead of library allocations.
 // Layout: [0, 4) work-queue counter, [64, 96) the four call totals, [256, ...) per-cell accepted
 // step counts, then per-cell rejection counts, for at most kNoAllocMaxCells cells (2 MiB).
@@ -672,6 +750,8 @@ struct chem_mech {
   int64_t cap_cells = 0;
   void* d_stage = nullptr;  // device staging for host-pointer calls
   size_t cap_stage = 0;
+  void* d_map_ws = nullptr;  // reference-mapping workspace
+  size_t cap_map_ws = 0;
   double* d_adj_ws = nullptr;  // reverse-sweep workspace
   size_t cap_adj_ws = 0;
   int* d_adj_counters = nullptr;
@@ -1005,6 +1085,7 @@ void chem_free_mechanism(chem_mech* m) {
   cudaFree(m->d_stage);
   cudaFree(m->d_adj_ws);
   cudaFree(m->d_adj_counters);
+  cudaFree(m->d_map_ws);
   delete m;
 }
 
@@ -1164,6 +1245,86 @@ int chem_integrate(const chem_mech* m, double p_Pa, double* T, double* Y, int64_
                    double atol, double* h_inout, int32_t* status, const chem_opts* opts, chem_stats* stats,
                    void* stream) {
   return integrate_impl(m, p_Pa, T, Y, ncells, dt, rtol, atol, h_inout, status, opts, stats, stream, nullptr, 0);
+}
+
+int chem_integrate_mapped(const chem_mech* mc, double p_Pa, double* T, double* Y, int64_t ncells, double dt,
+                          double rtol, double atol, double* h_inout, int32_t* status, const double* refs,
+                          int32_t n_ref, double tol_T, double tol_Y, int32_t* zone, int64_t* n_mapped,
+                          const chem_opts* opts, chem_stats* stats, void* stream) {
+  chem_mech* m = const_cast<chem_mech*>(mc);
+  if (!m) return set_err(CHEM_EINVAL, "chem_integrate_mapped: NULL mechanism");
+  if (ncells < 0 || ncells > (int64_t)0x7fffffff) return set_err(CHEM_EINVAL, "chem_integrate_mapped: bad ncells");
+  if (n_ref < 0 || n_ref > 64 || (n_ref > 0 && !refs))
+    return set_err(CHEM_EINVAL, "chem_integrate_mapped: 0..64 reference states, host array");
+  if (!(tol_T >= 0.0) || !(tol_Y >= 0.0)) return set_err(CHEM_EINVAL, "chem_integrate_mapped: negative tolerance");
+  if (n_mapped) *n_mapped = 0;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (ncells == 0) return CHEM_OK;
+  if (!T || !Y) return set_err(CHEM_EINVAL, "chem_integrate_mapped: NULL argument");
+  const void* arrays[5] = {T, Y, h_inout, status, zone};
+  for (const void* ptr : arrays)
+    if (ptr && !is_device_ptr(ptr)) return set_err(CHEM_EINVAL, "chem_integrate_mapped: device arrays only");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int K = m->host.K;
+  const int64_t nc_max = ncells + n_ref;
+  // workspace: refs | count | zone | pos | list | Tc | Yc | hc | sc
+  size_t off = 0;
+  auto place = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+  const size_t o_refs = place(sizeof(double) * (size_t)std::max(n_ref, 1) * (1 + K));
+  const size_t o_cnt = place(sizeof(unsigned long long));
+  const size_t o_zone = place(sizeof(int32_t) * ncells);
+  const size_t o_pos = place(sizeof(int64_t) * ncells);
+  const size_t o_list = place(sizeof(int64_t) * ncells);
+  const size_t o_Tc = place(sizeof(double) * nc_max);
+  const size_t o_Yc = place(sizeof(double) * nc_max * K);
+  const size_t o_hc = place(sizeof(double) * nc_max);
+  const size_t o_sc = place(sizeof(int32_t) * nc_max);
+  if (off > m->cap_map_ws) {
+    cudaFree(m->d_map_ws);
+    m->d_map_ws = nullptr;
+    m->cap_map_ws = 0;
+    CK(cudaMalloc(&m->d_map_ws, off));
+    m->cap_map_ws = off;
+  }
+  char* b = static_cast<char*>(m->d_map_ws);
+  double* d_refs = reinterpret_cast<double*>(b + o_refs);
+  unsigned long long* d_cnt = reinterpret_cast<unsigned long long*>(b + o_cnt);
+  int32_t* d_zone = zone ? zone : reinterpret_cast<int32_t*>(b + o_zone);
+  int64_t* d_pos = reinterpret_cast<int64_t*>(b + o_pos);
+  int64_t* d_list = reinterpret_cast<int64_t*>(b + o_list);
+  double* Tc = reinterpret_cast<double*>(b + o_Tc);
+  double* Yc = reinterpret_cast<double*>(b + o_Yc);
+  double* hc = reinterpret_cast<double*>(b + o_hc);
+  int32_t* sc = reinterpret_cast<int32_t*>(b + o_sc);
+  if (n_ref > 0)
+    CK(cudaMemcpyAsync(d_refs, refs, sizeof(double) * (size_t)n_ref * (1 + K), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), st));
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((ncells + threads - 1) / threads);
+  map_classify_kernel<<<blocks, threads, 0, st>>>(T, Y, ncells, K, d_refs, n_ref, tol_T, tol_Y, d_zone, d_pos,
+                                                  d_list, d_cnt);
+  CK(cudaGetLastError());
+  unsigned long long n_un_u = 0;
+  CK(cudaMemcpyAsync(&n_un_u, d_cnt, sizeof(n_un_u), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));  // the solve's size is the number of cells left to solve
+  const int64_t n_un = (int64_t)n_un_u;
+  const int64_t nc = n_un + n_ref;
+  if (nc > 0) {
+    map_gather_kernel<<<(unsigned)((nc + threads - 1) / threads), threads, 0, st>>>(T, Y, h_inout, ncells, K, d_refs,
+                                                                                   n_ref, d_list, n_un, Tc, Yc, hc);
+    CK(cudaGetLastError());
+    chem_opts o;
+    chem_default_opts(&o);
+    if (opts) o = *opts;
+    o.use_graph = 0;  // the compact arrays' size changes from call to call
+    const int rc = integrate_impl(m, p_Pa, Tc, Yc, nc, dt, rtol, atol, hc, sc, &o, stats, stream, nullptr, 0);
+    if (rc) return rc;
+  }
+  map_scatter_kernel<<<blocks, threads, 0, st>>>(T, Y, h_inout, status, ncells, K, d_refs, d_zone, d_pos, n_un, n_ref,
+                                                 Tc, Yc, hc, sc);
+  CK(cudaGetLastError());
+  if (n_mapped) *n_mapped = ncells - n_un;
+  return CHEM_OK;
 }
 
 int chem_integrate_record(const chem_mech* m, double p_Pa, double* T, double* Y, int64_t ncells, double dt,

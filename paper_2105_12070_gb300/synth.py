@@ -344,14 +344,24 @@ def cells_uniform(seed: int, K: int, n: int, T_range=(1000.0, 1800.0)):
     return T, Y
 
 
+def _shear_streams(rng, K):
+    return rng.dirichlet(np.ones(K)), rng.dirichlet(np.ones(K))
+
+
+def shear_layer_streams(seed: int, K: int, T_fuel: float = 800.0, T_ox: float = 1500.0):
+    """The two unmixed streams of cells_shear_layer (the same seeded draws): (T, Y [K]) of the
+    fuel (Z = 1) and of the oxidiser (Z = 0), the ambient states far from the layer."""
+    Y_fuel, Y_ox = _shear_streams(np.random.default_rng(seed), K)
+    return (T_fuel, Y_fuel), (T_ox, Y_ox)
+
+
 def cells_shear_layer(seed: int, K: int, nx: int = 256, ny: int = 256, delta: float = 8.0,
                       T_fuel: float = 800.0, T_ox: float = 1500.0):
     """2-D shear-layer field: Z = (1 + tanh(y/delta))/2 with a seeded sinusoidal displacement of
     5% of the height; T and Y mixed linearly in Z between two Dirichlet(1) streams (Z = 1 is fuel).
     Cells are ordered row-major (c = j*nx + i).  Returns T [n], Y [K, n], Z [n]."""
     rng = np.random.default_rng(seed)
-    Y_fuel = rng.dirichlet(np.ones(K))
-    Y_ox = rng.dirichlet(np.ones(K))
+    Y_fuel, Y_ox = _shear_streams(rng, K)
     m = int(rng.integers(1, 5))
     phi = rng.uniform(0.0, 2.0 * np.pi)
     i = np.arange(nx)[None, :]
@@ -375,7 +385,7 @@ def workload_shear_layer(n_side: int = 256):
     mech = mechanism_53()
     T, Y, _ = cells_shear_layer(102, mech.K, n_side, n_side)
     return dict(name=f"mech53_shear{n_side}x{n_side}", mech=mech, p_Pa=40.0 * P_ATM_PA, T=T, Y=Y, dt=1e-5,
-                rtol=1e-6, atol=1e-10)
+                rtol=1e-6, atol=1e-10, streams=shear_layer_streams(102, mech.K))
 
 
 def workload_0d(n: int = 608):
