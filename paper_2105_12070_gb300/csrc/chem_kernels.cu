@@ -51,6 +51,12 @@ __device__ unsigned long long g_phase_cycles[8];
 // ------------------------------------------------------------------------------------------
 // Kernels
 
+// Threads per CTA of the integrate kernels (8 warps: with ~230 registers per thread that is the
+// register file, and shared memory holds 4 cells of 53 species)
+#ifndef CHEM_MAX_THREADS_PER_CTA
+#define CHEM_MAX_THREADS_PER_CTA 256
+#endif
+
 struct IntegrateArgs {
   double p, dt, rtol, atol;
   double *T, *Y;
@@ -201,7 +207,7 @@ __device__ inline int64_t next_cell(const IntegrateArgs& a, const Grp<G>& g, con
 }
 
 template <int G>
-__global__ void __launch_bounds__(256, 1) integrate_kernel(DevMech m, Plan plan, IntegrateArgs a) {
+__global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) integrate_kernel(DevMech m, Plan plan, IntegrateArgs a) {
   extern __shared__ double smem[];
   Grp<G> g;
   g.t = threadIdx.x % Grp<G>::NT;
@@ -411,7 +417,7 @@ __device__ inline double seulex_work(int j) {
 }
 
 template <int G>
-__global__ void __launch_bounds__(256, 1) seulex_kernel(DevMech m, Plan plan, IntegrateArgs a) {
+__global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) seulex_kernel(DevMech m, Plan plan, IntegrateArgs a) {
   extern __shared__ double smem[];
   Grp<G> g;
   g.t = threadIdx.x % Grp<G>::NT;
@@ -867,7 +873,8 @@ int pick_launch(const chem_mech* m, int64_t ncells, int want_G, int want_cpc, in
   L.G = G;
   L.plan = make_plan(m->host.K, m->host.R, m->dev.n_pd, G);
   const size_t per_cell = (size_t)L.plan.total * sizeof(double);
-  int max_cpc = (int)std::min<size_t>(std::max(1, std::min(8 / G, 15)), m->max_smem / per_cell);
+  int max_cpc = (int)std::min<size_t>(std::max(1, std::min(CHEM_MAX_THREADS_PER_CTA / 32 / G, 15)),
+                                      m->max_smem / per_cell);
   if (max_cpc < 1)
     return set_err(CHEM_ESIZE, "mechanism working set (" + std::to_string(per_cell) +
                                    " B per cell) exceeds the shared memory of one CTA");
