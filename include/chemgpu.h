@@ -148,6 +148,14 @@ int chem_integrate_noalloc(const chem_mech* mech, double p_Pa, double* T, double
                            double rtol, double atol, double* h_inout, int32_t* status, int32_t* steps,
                            int32_t* rejects, const chem_opts* opts, chem_stats* stats, void* stream);
 
+/* chem_integrate with a pressure per cell: p_Pa[ncells] (Pa) instead of one value, for flow
+ * solvers whose cells sit at different pressures (the constant-pressure system of Eq. 1 holds
+ * within each cell over dt).  Device arrays only.  A cell whose pressure is not positive and
+ * finite reports CHEM_CELL_BAD_INPUT. */
+int chem_integrate_varp(const chem_mech* mech, const double* p_Pa, double* T, double* Y, int64_t ncells, double dt,
+                        double rtol, double atol, double* h_inout, int32_t* status, const chem_opts* opts,
+                        chem_stats* stats, void* stream);
+
 /* chem_integrate with zonal reference-cell mapping (DLBFoam's, Sec. 2.2): a cell whose state
  * lies within |T - T_r| <= tol_T and max_k |Y_k - Y_r,k| <= tol_Y of reference state r (an ambient
  * zone of low reactivity; the first such r) is not solved: it receives that reference's change

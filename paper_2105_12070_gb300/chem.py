@@ -81,12 +81,14 @@ def load_library(build_if_missing: bool = True):
         lib.chem_integrate_mapped.argtypes = [vp, dp, vp, vp, i64, dp, dp, dp, vp, vp, vp, ctypes.c_int32, dp, dp,
                                               vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ChemOpts),
                                               ctypes.POINTER(ChemStats), vp]
+        lib.chem_integrate_varp.argtypes = [vp, vp, vp, vp, i64, dp, dp, dp, vp, vp, ctypes.POINTER(ChemOpts),
+                                            ctypes.POINTER(ChemStats), vp]
         lib.chem_get_lnA.argtypes = [vp, vp]
         lib.chem_set_lnA.argtypes = [vp, vp]
         for name in ("chem_load_mechanism", "chem_mech_dims", "chem_rates", "chem_jacobian", "chem_integrate",
                      "chem_last_cell_counters", "chem_probe_fp64_peak", "chem_integrate_noalloc",
                      "chem_debug_exp", "chem_integrate_record", "chem_adjoint", "chem_get_lnA", "chem_set_lnA",
-                     "chem_integrate_mapped"):
+                     "chem_integrate_mapped", "chem_integrate_varp"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -280,6 +282,25 @@ def chem_adjoint(mech: Mechanism, p_Pa: float, rec, nsteps, status, gT, gY, gT0,
     pgC, _ = _ptr(g_lnA_cells, np.float64)
     _check(mech._lib.chem_adjoint(mech.handle, float(p_Pa), n, ptrs[0], int(rec.shape[1]), pn, ps, pgT, pgY, pgT0,
                                   pgY0, pgA, pgC, _stream(stream, dev)))
+
+
+def chem_integrate_varp(mech: Mechanism, p_Pa, T, Y, dt: float, rtol: float = 1e-6, atol: float = 1e-10,
+                        h_inout=None, status=None, opts: ChemOpts | None = None, want_stats: bool = False,
+                        stream=None):
+    """chem_integrate with a pressure per cell (p_Pa: (ncells,) float64, Pa); device tensors only."""
+    n = _cells(mech, T, Y)
+    if tuple(p_Pa.shape) != (n,):
+        raise ValueError(f"p_Pa must have shape (ncells={n},)")
+    pp, _ = _ptr(p_Pa, np.float64)
+    pT, dT = _ptr(T, np.float64)
+    pY, _ = _ptr(Y, np.float64)
+    ph, _ = _ptr(h_inout, np.float64)
+    ps, _ = _ptr(status, np.int32)
+    st = ChemStats() if want_stats else None
+    _check(mech._lib.chem_integrate_varp(mech.handle, pp, pT, pY, n, float(dt), float(rtol), float(atol), ph, ps,
+                                         ctypes.byref(opts) if opts is not None else None,
+                                         ctypes.byref(st) if st is not None else None, _stream(stream, dT)))
+    return st
 
 
 def chem_integrate_mapped(mech: Mechanism, p_Pa: float, T, Y, dt: float, refs, tol_T: float, tol_Y: float,

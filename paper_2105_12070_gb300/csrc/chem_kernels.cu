@@ -77,6 +77,7 @@ struct IntegrateArgs {
   int rec_cap;        // checkpoints per cell
   int solver;         // CHEM_SOLVER_*
   int fdjac;          // forward-difference Jacobian instead of the analytical one
+  const double* p_cells;  // per-cell pressure in Pa (NULL: p for every cell)
 };
 
 // First-order forward-difference Jacobian (the alternative the paper measures the analytical
@@ -231,7 +232,8 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) integrate_kernel(
       w.y[i] = v;
       bad |= !isfinite(v);
     }
-    bad = (g.sum((double)bad) > 0.0) || !(a.T[cell] > 0.0);
+    const double pc = a.p_cells ? 10.0 * a.p_cells[cell] : a.p;  // dyn/cm^2
+    bad = (g.sum((double)bad) > 0.0) || !(a.T[cell] > 0.0) || !(pc > 0.0 && pc < INFINITY);
     int status = bad ? CHEM_CELL_BAD_INPUT : CHEM_CELL_OK;
     int nsteps = 0, nrej = 0;
     double h_next = 0.01 * a.dt;
@@ -249,9 +251,9 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) integrate_kernel(
       PHASE_BEGIN
       if (need_jac) {
         if (a.fdjac) {
-          cell_fd_jacobian(m, g, a.p, w);
+          cell_fd_jacobian(m, g, pc, w);
         } else {
-          const CellScalars s0 = cell_rates(m, g, a.p, w.y, w.f0, eval_mem(w), w.A, true);
+          const CellScalars s0 = cell_rates(m, g, pc, w.y, w.f0, eval_mem(w), w.A, true);
           PHASE_END(0);
           cell_jacobian(m, g, s0, w.f0, eval_mem(w), w.A, w.B);
         }
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) integrate_kernel(
         if (conv) {
           for (int i = g.t; i < N; i += NT) w.ynew[i] = fma(c_a21, w.u[0][i], w.y[i]);
           g.sync();
-          cell_rates(m, g, a.p, w.ynew, w.fs, eval_mem(w), (double*)nullptr, false);
+          cell_rates(m, g, pc, w.ynew, w.fs, eval_mem(w), (double*)nullptr, false);
           PHASE_END(4);
           for (int i = g.t; i < N; i += NT) w.rhs[i] = fma(c_c21 * invh, w.u[0][i], w.fs[i]);
           g.sync();
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) integrate_kernel(
         if (conv) {
           for (int i = g.t; i < N; i += NT) w.ynew[i] = w.y[i] + c_a31 * w.u[0][i] + c_a32 * w.u[1][i];
           g.sync();
-          cell_rates(m, g, a.p, w.ynew, w.fs, eval_mem(w), (double*)nullptr, false);
+          cell_rates(m, g, pc, w.ynew, w.fs, eval_mem(w), (double*)nullptr, false);
           PHASE_END(4);
           for (int i = g.t; i < N; i += NT)
             w.rhs[i] = w.fs[i] + invh * (c_c31 * w.u[0][i] + c_c32 * w.u[1][i]);
@@ -447,7 +449,8 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) seulex_kernel(Dev
       w.y[i] = v;
       bad |= !isfinite(v);
     }
-    bad = (g.sum((double)bad) > 0.0) || !(a.T[cell] > 0.0);
+    const double pc = a.p_cells ? 10.0 * a.p_cells[cell] : a.p;  // dyn/cm^2
+    bad = (g.sum((double)bad) > 0.0) || !(a.T[cell] > 0.0) || !(pc > 0.0 && pc < INFINITY);
     int status = bad ? CHEM_CELL_BAD_INPUT : CHEM_CELL_OK;
     int nsteps = 0, nrej = 0;
     double H_next = 0.01 * a.dt;
@@ -463,7 +466,7 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) seulex_kernel(Dev
       if (attempt >= a.max_steps) { status = CHEM_CELL_MAX_STEPS; break; }
       if (H_next < 1e-14 * a.dt) { status = CHEM_CELL_H_UNDERFLOW; break; }
       if (need_jac) {
-        const CellScalars s0 = cell_rates(m, g, a.p, w.y, w.f0, eval_mem(w), w.A, true);
+        const CellScalars s0 = cell_rates(m, g, pc, w.y, w.f0, eval_mem(w), w.A, true);
         cell_jacobian(m, g, s0, w.f0, eval_mem(w), w.A, w.B);
         need_jac = false;
       }
@@ -483,7 +486,7 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) seulex_kernel(Dev
           const double* fsrc = w.f0;
           if (sub > 0) {
             g.sync();
-            cell_rates(m, g, a.p, yi, fi, eval_mem(w), (double*)nullptr, false);
+            cell_rates(m, g, pc, yi, fi, eval_mem(w), (double*)nullptr, false);
             fsrc = fi;
           }
           for (int i = g.t; i < N; i += NT) d[i] = fsrc[i];
@@ -1164,7 +1167,8 @@ int chem_jacobian(const chem_mech* m, double p_Pa, const double* T, const double
 
 static int integrate_impl(const chem_mech* mc, double p_Pa, double* T, double* Y, int64_t ncells, double dt,
                           double rtol, double atol, double* h_inout, int32_t* status, const chem_opts* opts,
-                          chem_stats* stats, void* stream, double* rec, int rec_cap) {
+                          chem_stats* stats, void* stream, double* rec, int rec_cap,
+                          const double* p_cells = nullptr) {
   chem_mech* m = const_cast<chem_mech*>(mc);
   if (ncells < 0) return set_err(CHEM_EINVAL, "chem_integrate: ncells < 0");
   if (!m || (ncells > 0 && (!T || !Y))) return set_err(CHEM_EINVAL, "chem_integrate: NULL argument");
@@ -1222,6 +1226,7 @@ static int integrate_impl(const chem_mech* mc, double p_Pa, double* T, double* Y
   a.rec = rec; a.rec_cap = rec_cap;
   a.solver = o.solver;
   a.fdjac = o.jacobian == CHEM_JAC_FD;
+  a.p_cells = p_cells;
   if (o.use_graph && dev) {
     rc = launch_via_graph(m, o, a, st);
   } else {
@@ -1252,6 +1257,23 @@ int chem_integrate(const chem_mech* m, double p_Pa, double* T, double* Y, int64_
                    double atol, double* h_inout, int32_t* status, const chem_opts* opts, chem_stats* stats,
                    void* stream) {
   return integrate_impl(m, p_Pa, T, Y, ncells, dt, rtol, atol, h_inout, status, opts, stats, stream, nullptr, 0);
+}
+
+int chem_integrate_varp(const chem_mech* m, const double* p_Pa, double* T, double* Y, int64_t ncells, double dt,
+                        double rtol, double atol, double* h_inout, int32_t* status, const chem_opts* opts,
+                        chem_stats* stats, void* stream) {
+  if (!m) return set_err(CHEM_EINVAL, "chem_integrate_varp: NULL mechanism");
+  if (ncells < 0) return set_err(CHEM_EINVAL, "chem_integrate_varp: ncells < 0");
+  if (ncells == 0) {
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    return CHEM_OK;
+  }
+  if (!p_Pa || !T || !Y) return set_err(CHEM_EINVAL, "chem_integrate_varp: NULL argument");
+  const void* arrays[5] = {p_Pa, T, Y, h_inout, status};
+  for (const void* ptr : arrays)
+    if (ptr && !is_device_ptr(ptr)) return set_err(CHEM_EINVAL, "chem_integrate_varp: device arrays only");
+  // the scalar pressure only passes the argument check; every cell uses its own p_Pa[c]
+  return integrate_impl(m, 1.0, T, Y, ncells, dt, rtol, atol, h_inout, status, opts, stats, stream, nullptr, 0, p_Pa);
 }
 
 int chem_integrate_mapped(const chem_mech* mc, double p_Pa, double* T, double* Y, int64_t ncells, double dt,
