@@ -118,7 +118,7 @@ __device__ inline EvalMem<S> adj_eval_mem(double* base, const AdjPlan& p) {
 
 template <int G>
 __device__ inline void solve_t(const Grp<G>& g, const AdjMem& w, int N, double* x) {
-  if (g.warp() == 0) warp_lu_solve_t(w.M, N, w.perm, w.invdiag, x, x);
+  if (g.warp() == g.lead) warp_lu_solve_t(w.M, N, w.perm, w.invdiag, x, x);
   g.sync();
 }
 
@@ -249,9 +249,7 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(DevMech m, AdjPlan plan
   extern __shared__ __align__(16) double smem[];
   constexpr int NT = Grp<G>::NT;
   Grp<G> g;
-  g.t = threadIdx.x % NT;
-  g.gid = threadIdx.x / NT;
-  g.parity = 0;
+  g.init(threadIdx.x % NT, threadIdx.x / NT);
   double* base = smem + (size_t)g.gid * plan.total;
   const AdjMem w = carve_adj(base, plan);
   g.red = w.red;

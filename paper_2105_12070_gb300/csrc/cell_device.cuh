@@ -123,6 +123,19 @@ struct Grp {
   int gid;      // group index in the CTA
   double* red;  // 6 G doubles of reduction scratch
   mutable int parity;
+  // The single-warp work of a cell (triangular solves) runs on its lead warp and the
+  // single-thread work of the LU (pivot reciprocals, the composed permutation) on its aux warp.
+  // Warp w of a CTA issues on SM sub-partition w % 4, so the groups that share sub-partitions
+  // take their lead warps on different ones: the FP64 pipes of all four carry the same load.
+  int lead, aux;
+
+  __device__ void init(int thread, int group) {
+    t = thread;
+    gid = group;
+    parity = 0;
+    lead = (G >= 4) ? group % G : (G == 2 ? (group >> 1) & 1 : 0);
+    aux = (G > 1) ? (lead + 1) % G : 0;
+  }
 
   __device__ int lane() const { return t & 31; }
   __device__ int warp() const { return t >> 5; }
@@ -837,8 +850,8 @@ __device__ bool cell_lu(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* in
       if (v > best) { best = v; bi = i; bv = (double)a; }
     }
     g.argmax(best, bi, bv);
-    // one thread takes the reciprocal of the pivot while the others swap the rows
-    if (g.t == 0) {
+    // one thread (of the aux warp) takes the reciprocal of the pivot while the others swap rows
+    if (g.t == 32 * g.aux) {
       piv[k] = bi;
       invdiag[k] = S(1) / S(bv);
     }
@@ -887,7 +900,7 @@ __device__ bool cell_lu(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* in
     g.sync();
   }
   // compose the row interchanges: row i of the factors is row perm[i] of the original matrix
-  if (g.t == 0) {
+  if (g.t == 32 * g.aux) {
     for (int i = 0; i < N; ++i) perm[i] = i;
     for (int k = 0; k < N; ++k) {
       const int p = piv[k];
@@ -1038,7 +1051,7 @@ __device__ void warp_lu_solve_t(const double* A, int N, const int* perm, const d
 template <int G>
 __device__ inline void cell_solve(const Grp<G>& g, const double* A, int N, const int* perm, const double* invdiag,
                                   double* x) {
-  if (g.warp() == 0) warp_lu_solve(A, N, perm, invdiag, x);
+  if (g.warp() == g.lead) warp_lu_solve(A, N, perm, invdiag, x);
   g.sync();
 }
 

@@ -159,7 +159,7 @@ __device__ bool stage_solve(const Grp<G>& g, const CellMem& w, const IntegrateAr
     return true;
   }
   const float* S = reinterpret_cast<const float*>(w.B);
-  if (g.warp() == 0) warp_lu_solve32(S, N, w.perm, w.invd32, w.er, w.ec, w.rhs, u);
+  if (g.warp() == g.lead) warp_lu_solve32(S, N, w.perm, w.invd32, w.er, w.ec, w.rhs, u);
   g.sync();
   double conv = INFINITY;
   for (int s = 0; s < a.refine_sweeps; ++s) {
@@ -176,7 +176,7 @@ __device__ bool stage_solve(const Grp<G>& g, const CellMem& w, const IntegrateAr
       w.res[i] = fma(-gh, u[i], w.rhs[i]) - (s0 + s1);
     }
     g.sync();
-    if (g.warp() == 0) warp_lu_solve32(S, N, w.perm, w.invd32, w.er, w.ec, w.res, w.res);
+    if (g.warp() == g.lead) warp_lu_solve32(S, N, w.perm, w.invd32, w.er, w.ec, w.res, w.res);
     g.sync();
     double c = 0.0;
     for (int i = g.t; i < N; i += NT) {
@@ -211,9 +211,7 @@ template <int G>
 __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) integrate_kernel(DevMech m, Plan plan, IntegrateArgs a) {
   extern __shared__ double smem[];
   Grp<G> g;
-  g.t = threadIdx.x % Grp<G>::NT;
-  g.gid = threadIdx.x / Grp<G>::NT;
-  g.parity = 0;
+  g.init(threadIdx.x % Grp<G>::NT, threadIdx.x / Grp<G>::NT);
   CellMem w = carve(smem + (size_t)g.gid * plan.total, plan);
   g.red = w.red;
   constexpr int NT = Grp<G>::NT;
@@ -329,7 +327,7 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) integrate_kernel(
         }
         g.sync();
         if (f32) {
-          if (g.warp() == 0)
+          if (g.warp() == g.lead)
             warp_lu_solve32(reinterpret_cast<const float*>(w.B), N, w.perm, w.invd32, w.er, w.ec, w.rhs, w.err);
           g.sync();
         } else {
@@ -422,9 +420,7 @@ template <int G>
 __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) seulex_kernel(DevMech m, Plan plan, IntegrateArgs a) {
   extern __shared__ double smem[];
   Grp<G> g;
-  g.t = threadIdx.x % Grp<G>::NT;
-  g.gid = threadIdx.x / Grp<G>::NT;
-  g.parity = 0;
+  g.init(threadIdx.x % Grp<G>::NT, threadIdx.x / Grp<G>::NT);
   CellMem w = carve(smem + (size_t)g.gid * plan.total, plan);
   g.red = w.red;
   constexpr int NT = Grp<G>::NT;
@@ -600,9 +596,7 @@ __global__ void __launch_bounds__(256, 1) rates_kernel(DevMech m, Plan plan, dou
                                                     int64_t ncells, double* out_f, double* out_J) {
   extern __shared__ double smem[];
   Grp<G> g;
-  g.t = threadIdx.x % Grp<G>::NT;
-  g.gid = threadIdx.x / Grp<G>::NT;
-  g.parity = 0;
+  g.init(threadIdx.x % Grp<G>::NT, threadIdx.x / Grp<G>::NT);
   CellMem w = carve(smem + (size_t)g.gid * plan.total, plan);
   g.red = w.red;
   constexpr int NT = Grp<G>::NT;
