@@ -504,6 +504,8 @@ def main():
                      "traffic": (TRAFFIC_BYTES_PER_CELL * n_total
                                  if (mech.K == 53 and prec == chem.CHEM_PREC_FP64 and rosen) else None),
                      "peak_source": peak["source"],
+                     "peak_measured": peak["measured_tflops"],
+                     "frac_of_measured": (achieved / peak["measured_tflops"] if np.isfinite(achieved) else None),
                      "flops_per_attempt": per["per_attempt"], "flops_per_accepted_step": per["per_accepted"]},
         "clocks": clk,
         "cells_status": {str(k): int(v) for k, v in zip(*np.unique(st_np, return_counts=True))},
@@ -604,11 +606,22 @@ def main():
     return 0
 
 
+# FP64 peak from unit counts and clocks: GB300's nominal FP64 rate (1.25 TFLOP/s) is 2 FP64 FMA
+# lanes per clock per SM (152 SMs x 2.07 GHz x 2 lanes x 2 flop = 1.259 TFLOP/s); one FP64 warp
+# instruction per 64 clocks per SM sub-partition
+FP64_LANES_PER_SM_CLK = 2
+N_SMS = 152
+SM_MAX_CLOCK_GHZ = 2.07
+
+
 def fp64_peak_tflops():
-    """FP64 FMA pipe peak, measured in this process on this GPU (chem_probe_fp64_peak: 8
-    independent DFMA chains per thread, 4 x 256 threads per SM)."""
+    """The roofline denominator of the FP64-ALU-bound kernels: derived from the unit count and
+    the maximum SM clock, with the DFMA throughput measured in this process beside it
+    (chem_probe_fp64_peak: 8 independent DFMA chains per thread, 4 x 256 threads per SM)."""
     from paper_2105_12070_gb300 import chem
-    return {"tflops": chem.chem_probe_fp64_peak(), "source": "measured in-process (DFMA microbenchmark)"}
+    derived = FP64_LANES_PER_SM_CLK * N_SMS * SM_MAX_CLOCK_GHZ * 2.0 / 1e3
+    return {"tflops": derived, "measured_tflops": chem.chem_probe_fp64_peak(),
+            "source": "derived: 2 FP64 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2 flop (nominal 1.25 TFLOP/s)"}
 
 
 if __name__ == "__main__":
