@@ -4,8 +4,9 @@ The whole 65 536-cell shear-layer field goes through one chem_integrate call wit
 benchmark's options (persistent kernel, device work queue, CUDA graph; automatic launch shape).
 The oracle integrates a sample of 32 cells spread over the field one by one, and the GPU values
 of those cells must match within the integrate tolerance 1e-6 |x| + 1e-10.  Every cell of the
-field must end with status OK, T and Y finite, and sum Y = 1 to 1e-12 (a property that holds at
-any size).  The discrete adjoint gets the same treatment at its benchmark size (16 384 igniting
+field must end with status OK, T and Y finite, sum Y = 1 to 1e-12 and its element totals kept to
+1e-12, and every 64th cell its mixture enthalpy kept to 2e-5 of its scale (properties of Eq. 1
+that hold at any size).  The discrete adjoint gets the same treatment at its benchmark size (16 384 igniting
 cells): the dot-product identity against the oracle's tangent-linear replay on two sampled cells.
 """
 import numpy as np
@@ -35,6 +36,20 @@ def test_full_shear_field_in_benchmark_configuration():
     assert np.all(st == 0)
     assert np.all(np.isfinite(Tg)) and np.all(np.isfinite(Yg))
     assert np.max(np.abs(Yg.sum(axis=0) - 1.0)) <= 1e-12
+    # invariants of Eq. 1 on every cell: element totals (linear invariants, kept by the method to
+    # rounding) and the mixture enthalpy at constant pressure (kept to the integration tolerance)
+    gen = w["mech"]
+    e0 = gen.comp.T @ (w["Y"] / gen.W[:, None])
+    e1 = gen.comp.T @ (Yg / gen.W[:, None])
+    assert np.max(np.abs(e1 - e0) / np.abs(e0).max(axis=0)) <= 1e-12
+    ru = 8.314462618e7
+    for c in range(0, n, 64):
+        h = []
+        for Tc, Yc in ((w["T"][c], w["Y"][:, c]), (Tg[c], Yg[:, c])):
+            _, hRT, _ = om.thermo(Tc)
+            hk = hRT * ru * Tc / gen.W
+            h.append(((Yc * hk).sum(), np.abs(Yc * hk).sum()))
+        assert abs(h[1][0] - h[0][0]) <= 2e-5 * h[0][1], c
     idx = np.random.default_rng(11).choice(n, size=32, replace=False)
     To, Yo, so, _, _ = om.integrate(w["p_Pa"], w["T"][idx], w["Y"][:, idx], w["dt"], w["rtol"], w["atol"],
                                     nthreads=16)
