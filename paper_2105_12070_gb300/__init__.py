@@ -1,7 +1,11 @@
 """GB300-native batched finite-rate chemistry solve (Morev et al., arXiv 2105.12070, Sec. 2.1-2.3).
 
 The compute path is the CUDA library libchemgpu.so (C ABI in include/chemgpu.h); `chem` is its
-thin Python binding and `synth` draws the seeded synthetic inputs.
+thin Python binding, `autograd` wraps the discrete adjoint in a torch.autograd.Function, `ranks`
+holds the multi-process helpers, `autotune` picks launch shapes, and `synth` draws the seeded
+synthetic inputs.
 """
-from .chem import (ChemError, ChemOpts, ChemStats, Mechanism, chem_integrate, chem_jacobian,  # noqa: F401
-                   chem_last_cell_counters, chem_load_mechanism, chem_rates, default_opts, load_library)
+from .chem import (ChemError, ChemOpts, ChemStats, Mechanism, chem_adjoint, chem_get_lnA,  # noqa: F401
+                   chem_integrate, chem_integrate_mapped, chem_integrate_noalloc, chem_integrate_record,
+                   chem_integrate_varp, chem_jacobian, chem_last_cell_counters, chem_load_mechanism, chem_rates,
+                   chem_set_lnA, default_opts, load_library)

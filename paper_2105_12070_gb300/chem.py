@@ -271,7 +271,7 @@ def chem_adjoint(mech: Mechanism, p_Pa: float, rec, nsteps, status, gT, gY, gT0,
         raise ValueError(f"g_lnA must have shape (R={mech.R},)")
     if g_lnA_cells is not None and tuple(g_lnA_cells.shape) != (n, mech.R):
         raise ValueError(f"g_lnA_cells must have shape (ncells={n}, R={mech.R})")
-    ptrs = [_ptr(x, np.float64)[0] for x in (rec,)]
+    prec, _ = _ptr(rec, np.float64)
     pn, dev = _ptr(nsteps, np.int32)
     ps, _ = _ptr(status, np.int32)
     pgT, _ = _ptr(gT, np.float64)
@@ -280,7 +280,7 @@ def chem_adjoint(mech: Mechanism, p_Pa: float, rec, nsteps, status, gT, gY, gT0,
     pgY0, _ = _ptr(gY0, np.float64)
     pgA, _ = _ptr(g_lnA, np.float64)
     pgC, _ = _ptr(g_lnA_cells, np.float64)
-    _check(mech._lib.chem_adjoint(mech.handle, float(p_Pa), n, ptrs[0], int(rec.shape[1]), pn, ps, pgT, pgY, pgT0,
+    _check(mech._lib.chem_adjoint(mech.handle, float(p_Pa), n, prec, int(rec.shape[1]), pn, ps, pgT, pgY, pgT0,
                                   pgY0, pgA, pgC, _stream(stream, dev)))
 
 
