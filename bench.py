@@ -72,6 +72,10 @@ def parse_args():
                     help="also time one launch per batch of this many cells (static assignment) against the queue")
     ap.add_argument("--autotune", action="store_true", help="pick warps/cell and cells/CTA with the autotuner first")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rtol", type=float, default=0.0, help="override the workload's rtol (work-precision runs)")
+    ap.add_argument("--accuracy-sample", type=int, default=0,
+                    help="error of the timed result on this many evenly spaced cells against a converged FP64 "
+                         "solve of the same cells (Rosenbrock at rtol 1e-10, atol 1e-14)")
     ap.add_argument("--map", action="store_true",
                     help="shear layer: zonal reference-cell mapping of the cells within 1e-9 of an unmixed "
                          "stream (chem_integrate_mapped), timed against the plain solve")
@@ -409,6 +413,9 @@ def main():
         w = synth.workload_shear_layer()
     if args.dt > 0:
         w["dt"] = args.dt
+    rtol_nominal = w["rtol"]
+    if args.rtol > 0:
+        w["rtol"] = args.rtol
     if args.impl == "reference":
         return run_reference(args, w, world, rank)
 
@@ -512,6 +519,27 @@ def main():
         "steps_per_cell": {"mean": float(steps_np.mean()), "max": int(steps_np.max()),
                            "rejects_mean": float(rej_np.mean())},
     }
+    if args.accuracy_sample > 0:
+        # a converged FP64 solution of sampled cells (tight tolerances) on the same GPU path
+        m_s = min(args.accuracy_sample, n_total)
+        sidx = np.linspace(0, n_total - 1, m_s).astype(np.int64)
+        Ts = torch.from_numpy(T_host.numpy()[sidx].copy()).cuda()
+        Ys = torch.from_numpy(Y_host.numpy()[:, sidx].copy()).cuda()
+        sst = torch.zeros(m_s, dtype=torch.int32, device="cuda")
+        aopts = chem.default_opts(max_steps=2000000)
+        chem.chem_integrate(mech, w["p_Pa"], Ts, Ys, w["dt"], 1e-10, 1e-14, status=sst, opts=aopts)
+        Tt, Yt = Ts.cpu().numpy(), Ys.cpu().numpy()
+        Tr, Yr = T_out.numpy()[sidx], Y_out.numpy()[:, sidx]
+        scT = w["atol"] + rtol_nominal * np.abs(Tt)
+        scY = w["atol"] + rtol_nominal * np.abs(Yt)
+        eT = np.abs(Tr - Tt) / scT
+        eY = np.abs(Yr - Yt) / scY
+        per_cell = np.maximum(eT, eY.max(axis=0))
+        line["accuracy"] = {"sample_cells": int(m_s), "reference": "GPU Rosenbrock FP64, rtol 1e-10, atol 1e-14",
+                            "reference_status_ok": bool(np.all(sst.cpu().numpy() == 0)),
+                            "units": f"atol + rtol |x| with the nominal rtol {rtol_nominal:g}",
+                            "max_err": float(per_cell.max()), "median_err": float(np.median(per_cell)),
+                            "max_rel_err_T": float((np.abs(Tr - Tt) / np.abs(Tt)).max())}
     if args.map and "streams" in w:
         (Tf, Yf), (To, Yo) = w["streams"]
         refs = np.array([np.concatenate([[Tf], Yf]), np.concatenate([[To], Yo])])
