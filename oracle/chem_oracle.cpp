@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cctype>
 #include <cmath>
 #include <complex>
 #include <cstdint>
@@ -34,6 +35,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <fstream>
+#include <map>
 #include <sstream>
 #include <string>
 #include <thread>
@@ -69,7 +71,318 @@ struct Mech {
   std::vector<std::vector<int>> nu;
 };
 
+// ----------------------------------------------------------------------------------------------
+// CHEMKIN-II input (the common subset; an independent reader of the same text the library
+// reads): ELEMENTS with optional /mass/, SPECIES, THERMO cards (name cols 1-18, elements
+// 25-44, T ranges 46-73, coefficients in 15-column fields, high range first), REACTIONS with
+// CAL/MOLE, KCAL/MOLE, JOULES/MOLE, KJOULES/MOLE or KELVINS; reversible equations, +M and (+M)
+// with LOW / TROE and NAME/eff/ lists.
+
+static std::string ck_up(std::string s) {
+  std::transform(s.begin(), s.end(), s.begin(), [](unsigned char c) { return (char)std::toupper(c); });
+  return s;
+}
+
+static std::string ck_strip(const std::string& s) {
+  size_t a = 0, b = s.size();
+  while (a < b && std::isspace((unsigned char)s[a])) ++a;
+  while (b > a && std::isspace((unsigned char)s[b - 1])) --b;
+  return s.substr(a, b - a);
+}
+
+static double ck_num(std::string t, bool& ok) {
+  for (char& c : t)
+    if (c == 'd' || c == 'D') c = 'e';
+  std::istringstream ss(t);
+  double v = 0.0;
+  ss >> v;
+  ok = !ss.fail() && (ss >> std::ws).eof();
+  return v;
+}
+
+static bool load_chemkin(const char* path, Mech& m, std::string& err) {
+  std::ifstream in(path);
+  if (!in) { err = std::string("cannot open ") + path; return false; }
+  std::vector<std::string> L;
+  for (std::string l; std::getline(in, l);) {
+    const size_t bang = l.find('!');
+    if (bang != std::string::npos) l.erase(bang);
+    while (!l.empty() && (l.back() == '\r')) l.pop_back();
+    L.push_back(l);
+  }
+  auto head = [&](const std::string& l) {
+    std::istringstream ss(l);
+    std::string w;
+    ss >> w;
+    return ck_up(w).substr(0, 4);
+  };
+  std::vector<std::string> elements, species;
+  std::vector<double> mass;
+  std::map<std::string, int> idx;
+  std::vector<int> have;
+  bool ok = true;
+  size_t i = 0;
+  // ELEMENTS, SPECIES: tokens up to END
+  auto tokens_until_end = [&](std::string text) {
+    std::vector<std::string> out;
+    for (;;) {
+      std::istringstream ss(text);
+      for (std::string w; ss >> w;) {
+        if (ck_up(w) == "END") return out;
+        out.push_back(w);
+      }
+      if (++i >= L.size()) return out;
+      const std::string h = head(L[i]);
+      if (h == "SPEC" || h == "THER" || h == "REAC") { --i; return out; }
+      text = L[i];
+    }
+  };
+  for (; i < L.size(); ++i) {
+    const std::string h = head(L[i]);
+    if (h.empty()) continue;
+    if (h == "ELEM") {
+      std::string rest = L[i].substr(L[i].find_first_not_of(" \t"));
+      rest = rest.substr(rest.find_first_of(" \t/") == std::string::npos ? rest.size() : rest.find_first_of(" \t/"));
+      std::string all;
+      for (const std::string& t : tokens_until_end(rest)) all += t + " ";
+      // symbols, each optionally followed by /mass/
+      for (size_t p = 0; p < all.size();) {
+        const char c = all[p];
+        if (std::isspace((unsigned char)c)) { ++p; continue; }
+        if (c == '/') {
+          const size_t q = all.find('/', p + 1);
+          if (q == std::string::npos || elements.empty()) { err = "bad element mass"; return false; }
+          mass.back() = ck_num(ck_strip(all.substr(p + 1, q - p - 1)), ok);
+          if (!ok) { err = "bad element mass"; return false; }
+          p = q + 1;
+          continue;
+        }
+        size_t q = p;
+        while (q < all.size() && !std::isspace((unsigned char)all[q]) && all[q] != '/') ++q;
+        const std::string e = ck_up(all.substr(p, q - p));
+        elements.push_back(e);
+        const double m0 = e == "H" ? 1.00797 : e == "C" ? 12.01115 : e == "O" ? 15.9994 : e == "N" ? 14.0067
+                        : e == "AR" ? 39.948 : e == "HE" ? 4.0026 : 0.0;
+        mass.push_back(m0);
+        p = q;
+      }
+    } else if (h == "SPEC") {
+      std::string rest = L[i].substr(L[i].find_first_not_of(" \t"));
+      rest = rest.substr(std::min(rest.size(), rest.find_first_of(" \t")));
+      for (const std::string& t : tokens_until_end(rest)) {
+        if (idx.count(ck_up(t))) { err = "duplicate species " + t; return false; }
+        idx[ck_up(t)] = (int)species.size();
+        species.push_back(t);
+      }
+    } else if (h == "THER") {
+      m.K = (int)species.size();
+      m.E = (int)elements.size();
+      for (double x : mass)
+        if (!(x > 0)) { err = "element without a mass"; return false; }
+      m.W.assign(m.K, 0.0);
+      m.Tmid.assign(m.K, 1000.0);
+      m.comp.assign(m.K, std::vector<int>(m.E, 0));
+      m.alow.assign(m.K, std::vector<double>(7));
+      m.ahigh.assign(m.K, std::vector<double>(7));
+      have.assign(m.K, 0);
+      double tmid_default = 1000.0;
+      size_t j = i + 1;
+      if (j < L.size() && !(L[j].size() >= 80 && L[j][79] == '1')) {
+        std::istringstream ss(L[j]);
+        double a, b, c;
+        if (ss >> a >> b >> c) { tmid_default = b; ++j; }
+      }
+      for (; j < L.size(); ++j) {
+        if (head(L[j]) == "END") break;
+        if (!(L[j].size() >= 80 && L[j][79] == '1')) continue;
+        if (j + 3 >= L.size()) { err = "truncated thermo card"; return false; }
+        std::istringstream ns(L[j].substr(0, 18));
+        std::string name;
+        ns >> name;
+        auto it = idx.find(ck_up(name));
+        if (it == idx.end()) { j += 3; continue; }
+        const int k = it->second;
+        for (int e = 0; e < 4; ++e) {
+          const std::string sym = ck_up(ck_strip(L[j].substr(24 + 5 * e, 2)));
+          if (sym.empty()) continue;
+          const double n = ck_num(ck_strip(L[j].substr(26 + 5 * e, 3)), ok);
+          if (!ok) { err = "bad element count for " + name; return false; }
+          const auto pos = std::find(elements.begin(), elements.end(), sym);
+          if (pos == elements.end()) {
+            if (n != 0) { err = "undeclared element " + sym; return false; }
+            continue;
+          }
+          m.comp[k][pos - elements.begin()] += (int)std::lround(n);
+        }
+        const std::string tm = L[j].size() >= 73 ? ck_strip(L[j].substr(65, 8)) : std::string();
+        m.Tmid[k] = tm.empty() ? tmid_default : ck_num(tm, ok);
+        if (!ok) { err = "bad Tmid for " + name; return false; }
+        std::vector<double> a;
+        for (int r = 1; r <= 3; ++r)
+          for (int f = 0; f < 5 && (int)a.size() < 14; ++f) {
+            if ((int)L[j + r].size() < 15 * (f + 1)) { err = "short thermo card for " + name; return false; }
+            a.push_back(ck_num(ck_strip(L[j + r].substr(15 * f, 15)), ok));
+            if (!ok) { err = "bad thermo coefficient for " + name; return false; }
+          }
+        for (int q = 0; q < 7; ++q) { m.ahigh[k][q] = a[q]; m.alow[k][q] = a[7 + q]; }
+        have[k] = 1;
+        j += 3;
+      }
+      for (int k = 0; k < m.K; ++k) {
+        if (!have[k]) { err = "no thermo data for " + species[k]; return false; }
+        for (int e = 0; e < m.E; ++e) m.W[k] += m.comp[k][e] * mass[e];
+      }
+      i = j;
+    } else if (h == "REAC") {
+      double to_cal = 1.0;
+      {
+        std::istringstream ss(L[i]);
+        std::string w;
+        ss >> w;
+        while (ss >> w) {
+          const std::string u = ck_up(w);
+          if (u == "KCAL/MOLE") to_cal = 1000.0;
+          else if (u == "JOULES/MOLE") to_cal = 1.0 / 4.184;
+          else if (u == "KJOULES/MOLE") to_cal = 1000.0 / 4.184;
+          else if (u == "KELVINS") to_cal = kRc;
+          else if (u != "CAL/MOLE" && u != "MOLES") { err = "unsupported unit " + w; return false; }
+        }
+      }
+      for (++i; i < L.size(); ++i) {
+        const std::string l = ck_strip(L[i]);
+        if (l.empty()) continue;
+        if (head(l) == "END") break;
+        if (l.find('=') != std::string::npos) {
+          std::istringstream ss(l);
+          std::vector<std::string> t;
+          for (std::string w; ss >> w;) t.push_back(w);
+          if (t.size() < 4) { err = "bad reaction: " + l; return false; }
+          Reaction x;
+          bool o1, o2, o3;
+          x.A = ck_num(t[t.size() - 3], o1);
+          x.b = ck_num(t[t.size() - 2], o2);
+          x.Ea = ck_num(t[t.size() - 1], o3) * to_cal;
+          if (!(o1 && o2 && o3)) { err = "bad Arrhenius parameters: " + l; return false; }
+          std::string eq;
+          for (size_t q = 0; q + 3 < t.size(); ++q) eq += ck_up(t[q]);
+          std::string lhs, rhs;
+          if (eq.find("<=>") != std::string::npos) {
+            lhs = eq.substr(0, eq.find("<=>"));
+            rhs = eq.substr(eq.find("<=>") + 3);
+          } else if (eq.find("=>") != std::string::npos) {
+            err = "irreversible reactions are not supported: " + eq;
+            return false;
+          } else {
+            lhs = eq.substr(0, eq.find('='));
+            rhs = eq.substr(eq.find('=') + 1);
+          }
+          int kind[2] = {0, 0};  // 1: +M, 2: (+M)
+          std::vector<int> mols[2];
+          std::string sides[2] = {lhs, rhs};
+          for (int sd = 0; sd < 2; ++sd) {
+            std::string sv = sides[sd];
+            if (sv.size() >= 4 && sv.substr(sv.size() - 4) == "(+M)") {
+              kind[sd] = 2;
+              sv.erase(sv.size() - 4);
+            } else if (sv.find("(+") != std::string::npos) {
+              err = "specific collider not supported: " + eq;
+              return false;
+            }
+            std::stringstream ts(sv);
+            for (std::string term; std::getline(ts, term, '+');) {
+              if (term.empty()) { err = "empty term in " + eq; return false; }
+              if (term == "M") { kind[sd] = 1; continue; }
+              int coef = 1;
+              size_t d = 0;
+              while (d < term.size() && std::isdigit((unsigned char)term[d])) ++d;
+              if (d) coef = std::stoi(term.substr(0, d));
+              auto it = idx.find(term.substr(d));
+              if (it == idx.end()) { err = "unknown species " + term.substr(d); return false; }
+              while (coef-- > 0) mols[sd].push_back(it->second);
+            }
+          }
+          if (kind[0] != kind[1]) { err = "unbalanced third body in " + eq; return false; }
+          for (int sd = 0; sd < 2; ++sd)
+            if (mols[sd].empty() || mols[sd].size() > 2) { err = "one or two molecules per side: " + eq; return false; }
+          x.reac[0] = mols[0][0]; x.reac[1] = mols[0].size() == 2 ? mols[0][1] : -1;
+          x.prod[0] = mols[1][0]; x.prod[1] = mols[1].size() == 2 ? mols[1][1] : -1;
+          x.type = kind[0] == 2 ? 2 : kind[0];
+          if (x.type >= 1) x.eff.assign(m.K, 1.0);
+          m.rx.push_back(x);
+          continue;
+        }
+        if (m.rx.empty()) { err = "auxiliary line before a reaction: " + l; return false; }
+        Reaction& x = m.rx.back();
+        const std::string ul = ck_up(l);
+        std::string key = ul.substr(0, ul.find_first_of(" /"));
+        auto between_slashes = [&]() {
+          std::vector<double> v;
+          const size_t a = l.find('/'), b = l.rfind('/');
+          if (a == std::string::npos || b <= a) return v;
+          std::istringstream ss(l.substr(a + 1, b - a - 1));
+          for (std::string w; ss >> w;) {
+            bool okw;
+            v.push_back(ck_num(w, okw));
+            if (!okw) return std::vector<double>();
+          }
+          return v;
+        };
+        if (key == "DUP" || key == "DUPLICATE") continue;
+        if (key == "LOW") {
+          const std::vector<double> v = between_slashes();
+          if (x.type < 2 || v.size() != 3) { err = "bad LOW: " + l; return false; }
+          x.A0 = v[0]; x.b0 = v[1]; x.Ea0 = v[2] * to_cal;
+        } else if (key == "TROE") {
+          const std::vector<double> v = between_slashes();
+          if (x.type < 2 || (v.size() != 3 && v.size() != 4)) { err = "bad TROE: " + l; return false; }
+          x.type = 3;
+          x.troe[0] = v[0]; x.troe[1] = v[1]; x.troe[2] = v[2];
+          x.troe[3] = v.size() == 4 ? v[3] : 1e30;
+        } else if (key == "REV" || key == "PLOG" || key == "SRI" || key == "HIGH" || key == "FORD" ||
+                   key == "RORD" || key == "CHEB") {
+          err = "unsupported keyword " + key;
+          return false;
+        } else {
+          if (x.type < 1) { err = "efficiencies without a third body: " + l; return false; }
+          // NAME/value/ pairs
+          std::string rest = l;
+          while (!ck_strip(rest).empty()) {
+            const size_t a = rest.find('/');
+            const size_t b = rest.find('/', a + 1);
+            if (a == std::string::npos || b == std::string::npos) { err = "bad efficiencies: " + l; return false; }
+            auto it = idx.find(ck_up(ck_strip(rest.substr(0, a))));
+            if (it == idx.end()) { err = "unknown species in efficiencies: " + l; return false; }
+            x.eff[it->second] = ck_num(ck_strip(rest.substr(a + 1, b - a - 1)), ok);
+            if (!ok) { err = "bad efficiency value: " + l; return false; }
+            rest = rest.substr(b + 1);
+          }
+        }
+      }
+    }
+  }
+  if (m.K < 2 || m.rx.empty()) { err = "need SPECIES, THERMO and REACTIONS"; return false; }
+  for (const Reaction& x : m.rx)
+    if (x.type >= 2 && !(x.A0 > 0)) { err = "fall-off reaction without LOW"; return false; }
+  m.R = (int)m.rx.size();
+  m.nu.assign(m.K, std::vector<int>(m.R, 0));
+  for (int r = 0; r < m.R; ++r)
+    for (int s = 0; s < 2; ++s) {
+      if (m.rx[r].reac[s] >= 0) m.nu[m.rx[r].reac[s]][r] -= 1;
+      if (m.rx[r].prod[s] >= 0) m.nu[m.rx[r].prod[s]][r] += 1;
+    }
+  return true;
+}
+
 static bool load_mech(const char* path, Mech& m, std::string& err) {
+  {
+    std::ifstream probe(path);
+    for (std::string l; std::getline(probe, l);) {
+      const std::string t = ck_strip(l);
+      if (t.empty() || t[0] == '#' || t[0] == '!') continue;
+      if (t.rfind("CHEMMECH", 0) != 0) return load_chemkin(path, m, err);
+      break;
+    }
+  }
   std::ifstream in(path);
   if (!in) { err = std::string("cannot open ") + path; return false; }
   std::vector<std::string> lines;

@@ -134,6 +134,70 @@ class Mechanism:
             fh.write("\n".join(lines) + "\n")
         return path
 
+    def rounded(self, digits: int = 9):
+        """A copy whose NASA coefficients carry `digits` significant digits (what the E15.8 fields of
+        a CHEMKIN thermo card hold), so that its CHEMMECH and CHEMKIN files describe the same
+        numbers."""
+        import copy
+        m = copy.deepcopy(self)
+        r = lambda a: np.array([float(f"{x:.{digits - 1}e}") for x in np.ravel(a)]).reshape(np.shape(a))
+        m.a_low, m.a_high = r(self.a_low), r(self.a_high)
+        m.W = self.comp @ self.element_mass
+        return m
+
+    def write_chemkin(self, path: str) -> str:
+        """The mechanism in CHEMKIN-II text: ELEMENTS (with their masses), SPECIES, THERMO (NASA-7
+        cards, four 80-column lines per species, E15.8 coefficient fields) and REACTIONS (CAL/MOLE,
+        MOLES; reversible '<=>', '+M' third bodies with efficiencies, '(+M)' fall-off with LOW and
+        TROE)."""
+        names = self.species_names()
+        f17 = lambda x: repr(float(x))
+        L = ["! synthetic mechanism, seed %d (CHEMKIN-II form)" % self.seed]
+        L.append("ELEMENTS " + " ".join(f"{e} /{f17(mm)}/" for e, mm in zip(self.elements, self.element_mass)))
+        L.append("END")
+        L.append("SPECIES")
+        for i in range(0, self.K, 8):
+            L.append(" ".join(names[i:i + 8]))
+        L.append("END")
+        L.append("THERMO ALL")
+        L.append(f"{T_LOW:10.3f}{T_MID:10.3f}{T_HIGH:10.3f}")
+        for k in range(self.K):
+            el = ""
+            for e, c in zip(self.elements, self.comp[k]):
+                el += f"{e:<2s}{int(c):3d}"
+            el = el.ljust(20)[:20]
+            head = f"{names[k]:<18s}{'SYN':6s}{el}G{T_LOW:10.3f}{T_HIGH:10.3f}{T_MID:8.2f}"
+            L.append(head.ljust(79) + "1")
+            co = list(self.a_high[k]) + list(self.a_low[k])
+            fmt = lambda x: f"{x:15.8E}"
+            L.append("".join(fmt(x) for x in co[0:5]).ljust(79) + "2")
+            L.append("".join(fmt(x) for x in co[5:10]).ljust(79) + "3")
+            L.append("".join(fmt(x) for x in co[10:14]).ljust(79) + "4")
+        L.append("END")
+        L.append("REACTIONS CAL/MOLE MOLES")
+        for r in range(self.R):
+            t = int(self.rtype[r])
+            lhs = [names[i] for i in self.reac[r] if i >= 0]
+            rhs = [names[i] for i in self.prod[r] if i >= 0]
+            if t == TYPE_THIRD_BODY:
+                lhs.append("M")
+                rhs.append("M")
+            eq = "+".join(lhs) + ("(+M)" if t >= TYPE_LINDEMANN else "") + "<=>" + "+".join(rhs) + \
+                ("(+M)" if t >= TYPE_LINDEMANN else "")
+            L.append(f"{eq:<40s} {f17(self.A[r])} {f17(self.b[r])} {f17(self.Ea[r])}")
+            if t >= TYPE_LINDEMANN:
+                L.append("    LOW / " + " ".join(f17(x) for x in self.low[r]) + " /")
+            if t == TYPE_TROE:
+                L.append("    TROE / " + " ".join(f17(x) for x in self.troe[r]) + " /")
+            if t >= TYPE_THIRD_BODY:
+                eff = self.eff[r]
+                for i in range(0, self.K, 6):
+                    L.append("    " + " ".join(f"{names[k]}/{f17(eff[k])}/" for k in range(i, min(self.K, i + 6))))
+        L.append("END")
+        with open(path, "w") as fh:
+            fh.write("\n".join(L) + "\n")
+        return path
+
     def write_temp(self) -> str:
         fd, path = tempfile.mkstemp(prefix=f"mech_s{self.seed}_", suffix=".txt")
         os.close(fd)
