@@ -563,7 +563,7 @@ def main():
                 (np.abs(Ym - Yr) / (w["atol"] + w["rtol"] * np.abs(Yr))).max()))}
     if args.vs_fp64:
         # the plain FP64 Rosenbrock path on the same field, for the comparison the precision and
-        # solver options are judged by (speed at the state the timed path produced)
+        # solver options are compared against (speed and the state it produces)
         T_ref, Y_ref = T_out.clone(), Y_out.clone()
         fopts = chem.default_opts(precision=chem.CHEM_PREC_FP64, solver=chem.CHEM_SOLVER_ROSENBROCK)
         fopts.use_graph = 1
