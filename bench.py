@@ -60,7 +60,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "ff"], default="fp64",
+                    help="linear solves: FP64, FP32 LU + FP64 refinement, or FP32-pair LU + FP64 refinement")
+    ap.add_argument("--refine-sweeps", type=int, default=-1, help="refinement sweeps per stage solve (mixed, ff)")
     ap.add_argument("--solver", choices=["rosenbrock", "seulex"], default="rosenbrock",
                     help="integrator: the 4-stage Rosenbrock method or the paper's Seulex")
     ap.add_argument("--cells", type=int, default=0, help="cells per rank (0 = the full 65536-cell field)")
@@ -313,6 +315,7 @@ def run_adjoint(args, world, rank, local):
         "gpu_launches": 4 * args.steps,
         "roofline": None,
         "clocks": clk,
+        **({"refinement": lowp_stats} if lowp_stats else {}),
         "cells_status": {str(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
     }
     if rank == 0:
@@ -438,7 +441,7 @@ def main():
     Y = torch.empty_like(Y_host, device="cuda")
     status = torch.zeros(n_total, dtype=torch.int32, device="cuda")
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
-    prec = chem.CHEM_PREC_MIXED if args.precision == "mixed" else chem.CHEM_PREC_FP64
+    prec = {"fp64": chem.CHEM_PREC_FP64, "mixed": chem.CHEM_PREC_MIXED, "ff": chem.CHEM_PREC_MIXED_FF}[args.precision]
     solver = chem.CHEM_SOLVER_SEULEX if args.solver == "seulex" else chem.CHEM_SOLVER_ROSENBROCK
     if args.autotune:
         from paper_2105_12070_gb300 import autotune
@@ -446,26 +449,34 @@ def main():
         opts.solver = solver
     else:
         opts = chem.default_opts(precision=prec, solver=solver)
+    if args.refine_sweeps >= 0:
+        opts.refine_sweeps = args.refine_sweeps
     opts.use_graph = 1
     stream = torch.cuda.current_stream()
 
-    def one_step(timed: bool):
+    lowp_stats = {}
+
+    def one_step(timed: bool, want_stats: bool = False):
         flush.fill_(1.0)  # L2 flush between steps (outside the events)
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         e[0].record(stream)
         T.copy_(T_host, non_blocking=True)
         Y.copy_(Y_host, non_blocking=True)
         e[1].record(stream)
-        chem.chem_integrate(mech, w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], status=status, opts=opts)
+        st = chem.chem_integrate(mech, w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], status=status, opts=opts,
+                                 want_stats=want_stats)
         e[2].record(stream)
+        if st is not None:
+            lowp_stats.update(attempts=int(st.steps + st.rejects), refine_fallbacks=int(st.refine_fallbacks))
         T_out.copy_(T, non_blocking=True)
         Y_out.copy_(Y, non_blocking=True)
         e[3].record(stream)
         e[3].synchronize()
         return e[1].elapsed_time(e[2]), e[0].elapsed_time(e[3])
 
-    for _ in range(args.warmup):
-        one_step(False)
+    for i in range(args.warmup):
+        # the last warm-up call of a mixed-precision run also reads the refinement fallbacks
+        one_step(False, want_stats=(i == args.warmup - 1 and prec != chem.CHEM_PREC_FP64))
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -495,9 +506,10 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": kern_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if prec == chem.CHEM_PREC_FP64 else "f64+f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": {chem.CHEM_PREC_FP64: "f64", chem.CHEM_PREC_MIXED: "f64+f32"}.get(prec, "f64+f32x2"), "data": "synthetic",
         "config": {"workload": w["name"], "cells": n_total, "species": mech.K, "reactions": mech.R, "dt_s": w["dt"],
                    "p_atm": w["p_Pa"] / 101325.0, "rtol": w["rtol"], "atol": w["atol"], "precision": args.precision,
+                   "refine_sweeps": opts.refine_sweeps if prec != chem.CHEM_PREC_FP64 else None,
                    "solver": args.solver,
                    "warps_per_cell": opts.warps_per_cell, "cells_per_cta": opts.cells_per_cta, "cuda_graph": True,
                    "scheduling": "persistent kernel + device work queue", "l2": "flushed between steps (256 MiB write)",
@@ -515,6 +527,7 @@ def main():
                      "frac_of_measured": (achieved / peak["measured_tflops"] if np.isfinite(achieved) else None),
                      "flops_per_attempt": per["per_attempt"], "flops_per_accepted_step": per["per_accepted"]},
         "clocks": clk,
+        **({"refinement": lowp_stats} if lowp_stats else {}),
         "cells_status": {str(k): int(v) for k, v in zip(*np.unique(st_np, return_counts=True))},
         "steps_per_cell": {"mean": float(steps_np.mean()), "max": int(steps_np.max()),
                            "rejects_mean": float(rej_np.mean())},

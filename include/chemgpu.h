@@ -47,7 +47,6 @@ extern "C" {
 #define CHEM_CELL_RECORD_FULL 4  /* chem_integrate_record: more accepted steps than max_steps_rec;
                                     the cell stops at its last recorded step */
 
-/* precision of the linear solves inside the Rosenbrock stages */
 /* integrators (chem_opts.solver) */
 #define CHEM_SOLVER_ROSENBROCK 0 /* 4-stage L-stable Rosenbrock method, order 4(3) (default) */
 #define CHEM_SOLVER_SEULEX 1     /* the paper's Seulex (Sec. 2.3): linearly implicit Euler with
@@ -59,15 +58,21 @@ extern "C" {
 #define CHEM_JAC_FD 1       /* first-order forward differences, N + 1 rate evaluations: the
                                alternative the paper measures the analytical Jacobian against */
 
-#define CHEM_PREC_FP64 0   /* FP64 LU and substitutions */
-#define CHEM_PREC_MIXED 1  /* FP32 LU + FP64-residual iterative refinement; rates, Kc, error
-                              norm, step control and state update stay FP64 */
+/* precision of the linear solves inside the Rosenbrock stages (chem_opts.precision) */
+#define CHEM_PREC_FP64 0     /* FP64 LU and substitutions */
+#define CHEM_PREC_MIXED 1    /* FP32 LU + FP64-residual iterative refinement; rates, Kc, error
+                                norm, step control and state update stay FP64 */
+#define CHEM_PREC_MIXED_FF 2 /* LU and substitutions in FP32 pairs (hi + lo, ~48 significand
+                                bits in FP32 arithmetic) + FP64-residual iterative refinement
+                                (refine_sweeps 0 takes the pair solve without refinement);
+                                the rest FP64 as for CHEM_PREC_MIXED */
 
 typedef struct chem_mech chem_mech; /* opaque */
 
 typedef struct {
-  int precision;     /* CHEM_PREC_FP64 (default) or CHEM_PREC_MIXED */
-  int refine_sweeps; /* mixed: FP64-residual refinement sweeps per stage solve (default 2, 1..4) */
+  int precision;     /* CHEM_PREC_FP64 (default), CHEM_PREC_MIXED or CHEM_PREC_MIXED_FF */
+  int refine_sweeps; /* mixed: FP64-residual refinement sweeps per stage solve (default 2;
+                        1..4 for CHEM_PREC_MIXED, 0..4 for CHEM_PREC_MIXED_FF) */
   int max_steps;     /* step attempts per cell per call (default 100000) */
   int use_queue;     /* 1 (default): persistent kernel pulling cells from a device work queue;
                         0: static round-robin assignment of cells to warps */

@@ -24,6 +24,7 @@ CHEM_JAC_ANALYTIC = 0
 CHEM_JAC_FD = 1
 CHEM_PREC_FP64 = 0
 CHEM_PREC_MIXED = 1
+CHEM_PREC_MIXED_FF = 2
 CELL_STATUS = {0: "ok", 1: "max_steps", 2: "h_underflow", 3: "bad_input", 4: "record_full"}
 CHEM_CELL_RECORD_FULL = 4
 

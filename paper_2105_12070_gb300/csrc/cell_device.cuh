@@ -200,6 +200,23 @@ struct Grp {
     for (int i = 1; i < G; ++i) s = nanmax(s, r[i]);
     return s;
   }
+  // max_nan of v, and whether any thread of the group has flag set (one exchange)
+  __device__ double max_nan_any(double v, bool& flag) const {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(kFull, v, o));
+    flag = __any_sync(kFull, flag);
+    if (G == 1) return v;
+    double* r = red + (parity & 1) * 3 * G;
+    parity++;
+    if (lane() == 0) { r[2 * warp()] = v; r[2 * warp() + 1] = flag ? 1.0 : 0.0; }
+    sync();
+    double s = r[0];
+    bool f = r[1] != 0.0;
+#pragma unroll
+    for (int i = 1; i < G; ++i) { s = nanmax(s, r[2 * i]); f = f || r[2 * i + 1] != 0.0; }
+    flag = f;
+    return s;
+  }
   // argmax of key (ties to the lowest index) over the group, carrying a value along
   __device__ void argmax(long long& key, int& idx, double& val) const {
 #pragma unroll
@@ -827,6 +844,85 @@ __device__ void cell_jacobian_vjp(const DevMech& m, const Grp<G>& g, const CellS
 }
 
 // ------------------------------------------------------------------------------------------
+// ------------------------------------------------------------------------------------------
+// FP32 pairs ("float-float"): a value hi + lo with |lo| <= ulp(hi) / 2 carries about 48
+// significand bits in FP32 arithmetic (Dekker 1971; Knuth's two-sum and the FMA two-product),
+// which GB300 issues at 64 times the FP64 rate.  The FP32 operations are the IEEE-rounded
+// intrinsics, so the compiler cannot contract them and the error-free transformations stay
+// exact.  Used for the factors and the substitutions of CHEM_PREC_MIXED_FF.
+struct FF {
+  float hi, lo;
+  FF() = default;
+  __device__ FF(float h, float l) : hi(h), lo(l) {}
+  // nearest pair to an FP64 value (hi = fl32(x), lo = fl32(x - hi); x - hi is exact in FP64)
+  __device__ explicit FF(double x) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - (double)hi);
+  }
+  __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+// s + e = a + b exactly (Knuth's two-sum; no ordering of |a|, |b| needed)
+__device__ inline void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// renormalise s + e (|s| >= |e|, Dekker's fast two-sum)
+__device__ inline FF ff_norm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return FF(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ inline FF operator-(FF a) { return FF(-a.hi, -a.lo); }
+__device__ inline FF operator*(FF a, FF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);  // exact error of the leading product
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return ff_norm(p, e);
+}
+__device__ inline FF& operator*=(FF& a, FF b) { return a = a * b; }
+// a b + c
+__device__ inline FF fma(FF a, FF b, FF c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float pe = fmaf(a.hi, b.hi, -p);
+  pe = fmaf(a.hi, b.lo, pe);
+  pe = fmaf(a.lo, b.hi, pe);
+  float s, e;
+  two_sum(c.hi, p, s, e);
+  e = __fadd_rn(e, __fadd_rn(c.lo, pe));
+  return ff_norm(s, e);
+}
+// 1 / a: the FP32 reciprocal of hi and one Newton correction r (1 - a r) in pair arithmetic
+__device__ inline FF ff_recip(FF a) {
+  const float r = 1.0f / a.hi;
+  float e = fmaf(-a.hi, r, 1.0f);
+  e = fmaf(-a.lo, r, e);
+  return ff_norm(r, __fmul_rn(r, e));
+}
+
+// warp broadcast of a value held by lane l
+__device__ inline double shfl(double v, int l) { return __shfl_sync(kFull, v, l); }
+__device__ inline float shfl(float v, int l) { return __shfl_sync(kFull, v, l); }
+__device__ inline FF shfl(FF v, int l) { return FF(__shfl_sync(kFull, v.hi, l), __shfl_sync(kFull, v.lo, l)); }
+
+// The pivot travels through the group's argmax as a double: the value itself for FP64 and
+// FP32 factors (exact), the bit pattern of the pair for FP32 pairs; lu_recip turns it into
+// the reciprocal in the factor type.
+__device__ inline double lu_carry(double a) { return a; }
+__device__ inline double lu_carry(float a) { return (double)a; }
+__device__ inline double lu_carry(FF a) { return __hiloint2double(__float_as_int(a.hi), __float_as_int(a.lo)); }
+template <typename S>
+__device__ inline S lu_recip(double c);
+template <>
+__device__ inline double lu_recip<double>(double c) { return 1.0 / c; }
+template <>
+__device__ inline float lu_recip<float>(double c) { return 1.0f / (float)c; }
+template <>
+__device__ inline FF lu_recip<FF>(double c) {
+  return ff_recip(FF(__int_as_float(__double2hiint(c)), __int_as_float(__double2loint(c))));
+}
+
 // Dense LU with partial pivoting (row interchanges, ties to the lowest row), in place, and the
 // substitutions that use it (Sec. 2.3: dense LU + back substitution).  Returns false on an
 // exactly zero pivot.
@@ -834,6 +930,7 @@ __device__ void cell_jacobian_vjp(const DevMech& m, const Grp<G>& g, const CellS
 // |a| as an ordered integer key (bit pattern of a non-negative float / double)
 __device__ inline long long abs_key(double a) { return __double_as_longlong(fabs(a)); }
 __device__ inline long long abs_key(float a) { return (long long)__float_as_int(fabsf(a)); }
+__device__ inline long long abs_key(FF a) { return (long long)__float_as_int(fabsf(a.hi)); }
 
 template <int G, typename S>
 __device__ bool cell_lu(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* invdiag) {
@@ -847,13 +944,13 @@ __device__ bool cell_lu(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* in
     for (int i = k + g.t; i < N; i += NT) {
       const S a = A[i * N + k];
       const long long v = abs_key(a);
-      if (v > best) { best = v; bi = i; bv = (double)a; }
+      if (v > best) { best = v; bi = i; bv = lu_carry(a); }
     }
     g.argmax(best, bi, bv);
     // one thread (of the aux warp) takes the reciprocal of the pivot while the others swap rows
     if (g.t == 32 * g.aux) {
       piv[k] = bi;
-      invdiag[k] = S(1) / S(bv);
+      invdiag[k] = lu_recip<S>(bv);
     }
     if (best <= 0) ok = false;  // zero column: singular
     if (bi != k) {
@@ -918,8 +1015,8 @@ __device__ bool cell_lu(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* in
 // still holds rows below (forward) or above (backward) the column, without shared-memory round
 // trips or barriers.  The slot loops are unrolled over compile-time bounds so that no FMA is
 // issued for a slot with no active row.  perm is the composed row permutation of the LU.
-// T is double (FP64 factors) or float (mixed precision; then b is scaled by 2^-er on entry and
-// the result by 2^-ec on exit, see form_and_factor32).
+// T is double (FP64 factors), float or FF (mixed precision; then b is scaled by 2^-er on entry
+// and the result by 2^-ec on exit, the equilibration of form_and_factor_low).
 template <int S, typename T>
 __device__ void warp_lu_solve_s(const T* A, int N, const int* perm, const T* invdiag, const int* er, const int* ec,
                                 const double* b, double* x) {
@@ -941,7 +1038,7 @@ __device__ void warp_lu_solve_s(const T* A, int N, const int* perm, const T* inv
   for (int jb = 0; jb < S; ++jb) {
     const int jend = min(32 * jb + 32, N - 1);
     for (int j = 32 * jb; j < jend; ++j) {
-      const T xj = __shfl_sync(kFull, xr[jb], j & 31);
+      const T xj = shfl(xr[jb], j & 31);
 #pragma unroll
       for (int s = jb; s < S; ++s) {
         const int i = lane + 32 * s;
@@ -953,7 +1050,7 @@ __device__ void warp_lu_solve_s(const T* A, int N, const int* perm, const T* inv
 #pragma unroll
   for (int jb = S - 1; jb >= 0; --jb) {
     for (int j = min(32 * jb + 31, N - 1); j >= 32 * jb; --j) {
-      const T xj = __shfl_sync(kFull, xr[jb], j & 31) * invdiag[j];
+      const T xj = shfl(xr[jb], j & 31) * invdiag[j];
       if (lane == (j & 31)) xr[jb] = xj;
 #pragma unroll
       for (int s = 0; s <= jb; ++s) {
@@ -981,13 +1078,6 @@ __device__ void warp_lu_solve_any(const T* A, int N, const int* perm, const T* i
 
 __device__ void warp_lu_solve(const double* A, int N, const int* perm, const double* invdiag, double* x) {
   warp_lu_solve_any<double>(A, N, perm, invdiag, nullptr, nullptr, x, x);
-}
-
-// Mixed precision: x <- W^-1 b through the FP32 factors of the equilibrated matrix
-// S = D_r W D_c (D_r, D_c powers of two): z = D_r b, S v = z in FP32, x = D_c v.
-__device__ void warp_lu_solve32(const float* A, int N, const int* perm, const float* invdiag, const int* er,
-                                const int* ec, const double* b, double* x) {
-  warp_lu_solve_any<float>(A, N, perm, invdiag, er, ec, b, x);
 }
 
 // x <- W^-T b with the factors of cell_lu (P W = L U, P the row permutation perm): W^T =

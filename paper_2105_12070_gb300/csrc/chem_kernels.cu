@@ -71,7 +71,7 @@ struct IntegrateArgs {
   int64_t count;
   int max_steps;
   int use_queue;
-  int mixed;          // FP32 factors + FP64-residual refinement
+  int mixed;          // 0: FP64 factors; 1: FP32 factors, 2: FP32 pairs (+ FP64-residual refinement)
   int refine_sweeps;  // refinement sweeps per stage solve (mixed)
   double* rec;        // record mode: checkpoint of every accepted step (NULL: off)
   int rec_cap;        // checkpoints per cell
@@ -110,26 +110,43 @@ __device__ void cell_fd_jacobian(const DevMech& m, const Grp<G>& g, double p, co
 #define CHEM_MIXED_FP64_RUN 16
 #endif
 
+// v 2^k for a power-of-two scaling whose result is at most 2 (an exponent-field add, no FP64
+// operation); zero when v is zero or subnormal or the result would be subnormal.
+__device__ inline double scale2(double v, int k) {
+  const long long b = __double_as_longlong(v);
+  const int ef = (int)((b >> 52) & 0x7ff);
+  if (ef == 0 || ef + k <= 0) return 0.0;
+  return __longlong_as_double(b + ((long long)k << 52));
+}
+
+template <typename L>
+__device__ inline L to_low(double v);
+template <>
+__device__ inline float to_low<float>(double v) { return __double2float_rn(v); }
+template <>
+__device__ inline FF to_low<FF>(double v) { return FF(v); }
+
 // Equilibrate W = I gh - J by powers of two (row exponents er, then column exponents ec, from
-// the largest entries) and factor S = D_r W D_c in FP32 in the first half of buffer B.
-template <int G>
-__device__ bool form_and_factor32(const Grp<G>& g, const CellMem& w, int N, double gh) {
+// the largest entries) and factor S = D_r W D_c in the low precision L (FP32 or FP32 pairs) in
+// buffer B; the reciprocal pivots go to invd.  The diagonal gh + (-J)_ii is formed once in FP64
+// (in the residual vector, free until the stage solves), so the scans only compare exponents.
+template <int G, typename L>
+__device__ bool form_and_factor_low(const Grp<G>& g, const CellMem& w, int N, double gh, L* invd) {
   constexpr int NT = Grp<G>::NT;
-  float* S = reinterpret_cast<float*>(w.B);
+  L* S = reinterpret_cast<L*>(w.B);
+  double* dg = w.res;
+  for (int i = g.t; i < N; i += NT) dg[i] = gh + w.A[i * N + i];
+  g.sync();
   for (int i = g.t; i < N; i += NT) {
     int mx = 0;
-    for (int j = 0; j < N; ++j) {
-      const double v = (i == j) ? gh + w.A[i * N + j] : w.A[i * N + j];
-      mx = max(mx, exp_field(v));
-    }
+    for (int j = 0; j < N; ++j) mx = max(mx, exp_field(i == j ? dg[i] : w.A[i * N + j]));
     w.er[i] = mx - 1023;
   }
   g.sync();
   for (int j = g.t; j < N; j += NT) {
     int mx = -2100;
     for (int i = 0; i < N; ++i) {
-      const double v = (i == j) ? gh + w.A[i * N + j] : w.A[i * N + j];
-      const int ef = exp_field(v);
+      const int ef = exp_field(i == j ? dg[j] : w.A[i * N + j]);
       if (ef > 0) mx = max(mx, ef - 1023 - w.er[i]);
     }
     w.ec[j] = (mx < -900) ? 0 : mx;
@@ -137,46 +154,62 @@ __device__ bool form_and_factor32(const Grp<G>& g, const CellMem& w, int N, doub
   g.sync();
   for (int e = g.t; e < N * N; e += NT) {
     const int i = e / N, j = e - (e / N) * N;
-    const double v = (i == j) ? gh + w.A[e] : w.A[e];
-    S[e] = (float)(v * pow2(-w.er[i] - w.ec[j]));
+    S[e] = to_low<L>(scale2(i == j ? dg[i] : w.A[e], -w.er[i] - w.ec[j]));
   }
   g.sync();
-  return cell_lu<G, float>(g, S, N, w.piv, w.perm, w.invd32);
+  return cell_lu<G, L>(g, S, N, w.piv, w.perm, invd);
 }
 
-// u <- W^-1 rhs.  FP64 factors: one solve.  FP32 factors: a solve, then up to refine_sweeps
-// sweeps of r = rhs - W u (FP64, with the FP64 Jacobian), u += W32^-1 r, until the last
-// correction is below 1e-5 of the error-control scale atol + rtol |y|.  Returns false if it
-// did not get there.
-template <int G>
-__device__ bool stage_solve(const Grp<G>& g, const CellMem& w, const IntegrateArgs& a, int N, double gh, bool f32,
-                            double* u) {
+// x <- W^-1 b through the low-precision factors of the equilibrated matrix S = D_r W D_c:
+// z = D_r b, S v = z, x = D_c v (one warp).
+template <typename L>
+__device__ inline void low_solve(const CellMem& w, int N, const L* invd, const double* b, double* x) {
+  warp_lu_solve_any<L>(reinterpret_cast<const L*>(w.B), N, w.perm, invd, w.er, w.ec, b, x);
+}
+__device__ inline const float* invd_of(const CellMem& w, float*) { return w.invd32; }
+__device__ inline const FF* invd_of(const CellMem& w, FF*) { return reinterpret_cast<const FF*>(w.invdiag); }
+
+// u <- W^-1 rhs with low-precision factors L: a solve, then up to refine_sweeps sweeps of
+// r = rhs - W u (FP64, with the FP64 Jacobian), u += W_L^-1 r, until the last correction is
+// below 1e-5 of the error-control scale atol + rtol |y|, or the residual of the sweep is at the
+// rounding level of FP64 arithmetic (every |r_i| <= 2^-45 max_j |W_ij| max_j |u_j|, which
+// covers the N <= 128 terms of a row; no further sweep can then improve u, which is as accurate
+// as an FP64 solve can be checked to be).  Returns false if neither happens.  FP32 pairs with
+// refine_sweeps = 0 take the first solve as it is.
+template <int G, typename L>
+__device__ bool stage_solve_low(const Grp<G>& g, const CellMem& w, const IntegrateArgs& a, int N, double gh,
+                                double* u) {
   constexpr int NT = Grp<G>::NT;
-  if (!f32) {
-    for (int i = g.t; i < N; i += NT) u[i] = w.rhs[i];
-    g.sync();
-    cell_solve(g, w.B, N, w.perm, w.invdiag, u);
-    return true;
-  }
-  const float* S = reinterpret_cast<const float*>(w.B);
-  if (g.warp() == g.lead) warp_lu_solve32(S, N, w.perm, w.invd32, w.er, w.ec, w.rhs, u);
+  const L* invd = invd_of(w, (L*)nullptr);
+  if (g.warp() == g.lead) low_solve<L>(w, N, invd, w.rhs, u);
   g.sync();
+  if (a.refine_sweeps == 0) return true;
   double conv = INFINITY;
   for (int s = 0; s < a.refine_sweeps; ++s) {
-    // residual r = rhs - W u = rhs - gh u + J u (the buffer holds -J)
+    // residual r = rhs - W u = rhs - gh u + J u (the buffer holds -J); the exponent scan of u
+    // and the row exponents er (|W_ij| < 2^(er_i + 1)) give the rounding level of each row
+    bool above = false;
     for (int i = g.t; i < N; i += NT) {
       const double* Ji = w.A + (size_t)i * N;
       double s0 = 0.0, s1 = 0.0;
+      int ue = 0;
       int j = 0;
       for (; j + 1 < N; j += 2) {
         s0 = fma(Ji[j], u[j], s0);
         s1 = fma(Ji[j + 1], u[j + 1], s1);
+        ue = max(ue, max(exp_field(u[j]), exp_field(u[j + 1])));
       }
-      if (j < N) s0 = fma(Ji[j], u[j], s0);
-      w.res[i] = fma(-gh, u[i], w.rhs[i]) - (s0 + s1);
+      if (j < N) {
+        s0 = fma(Ji[j], u[j], s0);
+        ue = max(ue, exp_field(u[j]));
+      }
+      const double r = fma(-gh, u[i], w.rhs[i]) - (s0 + s1);
+      w.res[i] = r;
+      // |r| < 2^(e_r - 1022) <= 2^-45 2^(er_i + 1) 2^(ue - 1022)  <=  e_r <= er_i + ue - 44
+      above = above || exp_field(r) > w.er[i] + ue - 44;
     }
     g.sync();
-    if (g.warp() == g.lead) warp_lu_solve32(S, N, w.perm, w.invd32, w.er, w.ec, w.res, w.res);
+    if (g.warp() == g.lead) low_solve<L>(w, N, invd, w.res, w.res);
     g.sync();
     double c = 0.0;
     for (int i = g.t; i < N; i += NT) {
@@ -184,10 +217,24 @@ __device__ bool stage_solve(const Grp<G>& g, const CellMem& w, const IntegrateAr
       u[i] += d;
       c = Grp<G>::nanmax(c, fabs(d) / (a.atol + a.rtol * fabs(w.y[i])));
     }
-    conv = g.max_nan(c);
+    conv = g.max_nan_any(c, above);
+    if (!above && conv == conv) conv = 0.0;  // residual at the FP64 rounding level
     if (conv <= 1e-5) break;
   }
   return conv <= 1e-5;
+}
+
+// u <- W^-1 rhs: FP64 factors (lowp 0: one solve), FP32 factors (1) or FP32 pairs (2).
+template <int G>
+__device__ bool stage_solve(const Grp<G>& g, const CellMem& w, const IntegrateArgs& a, int N, double gh, int lowp,
+                            double* u) {
+  constexpr int NT = Grp<G>::NT;
+  if (lowp == 1) return stage_solve_low<G, float>(g, w, a, N, gh, u);
+  if (lowp == 2) return stage_solve_low<G, FF>(g, w, a, N, gh, u);
+  for (int i = g.t; i < N; i += NT) u[i] = w.rhs[i];
+  g.sync();
+  cell_solve(g, w.B, N, w.perm, w.invdiag, u);
+  return true;
 }
 
 // Next cell of this group (an index into the arrays), or -1 when the launch's range is done.
@@ -266,10 +313,12 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) integrate_kernel(
       double err = INFINITY;
       // after a fallback the next attempts go straight to FP64 factors for a while
       for (int pass = (a.mixed && attempt >= f64_until) ? 0 : 1; pass < 2; ++pass) {
-        const bool f32 = pass == 0;
+        const int lowp = pass == 0 ? a.mixed : 0;
         bool ok;
-        if (f32) {
-          ok = form_and_factor32(g, w, N, gh);
+        if (lowp == 1) {
+          ok = form_and_factor_low<G, float>(g, w, N, gh, w.invd32);
+        } else if (lowp == 2) {
+          ok = form_and_factor_low<G, FF>(g, w, N, gh, reinterpret_cast<FF*>(w.invdiag));
         } else {
           for (int e = g.t; e < N * N; e += NT) w.B[e] = w.A[e];
           g.sync();
@@ -283,7 +332,7 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) integrate_kernel(
         // stage 1
         for (int i = g.t; i < N; i += NT) w.rhs[i] = w.f0[i];
         g.sync();
-        conv = stage_solve(g, w, a, N, gh, f32, w.u[0]);
+        conv = stage_solve(g, w, a, N, gh, lowp, w.u[0]);
         PHASE_END(3);
         // stage 2
         if (conv) {
@@ -293,7 +342,7 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) integrate_kernel(
           PHASE_END(4);
           for (int i = g.t; i < N; i += NT) w.rhs[i] = fma(c_c21 * invh, w.u[0][i], w.fs[i]);
           g.sync();
-          conv = stage_solve(g, w, a, N, gh, f32, w.u[1]);
+          conv = stage_solve(g, w, a, N, gh, lowp, w.u[1]);
           PHASE_END(3);
         }
         // stage 3
@@ -305,14 +354,14 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) integrate_kernel(
           for (int i = g.t; i < N; i += NT)
             w.rhs[i] = w.fs[i] + invh * (c_c31 * w.u[0][i] + c_c32 * w.u[1][i]);
           g.sync();
-          conv = stage_solve(g, w, a, N, gh, f32, w.u[2]);
+          conv = stage_solve(g, w, a, N, gh, lowp, w.u[2]);
         }
         // stage 4 (same argument as stage 3)
         if (conv) {
           for (int i = g.t; i < N; i += NT)
             w.rhs[i] = w.fs[i] + invh * (c_c41 * w.u[0][i] + c_c42 * w.u[1][i] + c_c43 * w.u[2][i]);
           g.sync();
-          conv = stage_solve(g, w, a, N, gh, f32, w.u[3]);
+          conv = stage_solve(g, w, a, N, gh, lowp, w.u[3]);
         }
         if (!conv) {
           if (g.t == 0) atomicAdd(&a.totals[3], 1ull);
@@ -326,9 +375,11 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) integrate_kernel(
           w.rhs[i] = c_e[0] * w.u[0][i] + c_e[1] * w.u[1][i] + c_e[2] * w.u[2][i] + c_e[3] * w.u[3][i];
         }
         g.sync();
-        if (f32) {
-          if (g.warp() == g.lead)
-            warp_lu_solve32(reinterpret_cast<const float*>(w.B), N, w.perm, w.invd32, w.er, w.ec, w.rhs, w.err);
+        if (lowp == 1) {
+          if (g.warp() == g.lead) low_solve<float>(w, N, w.invd32, w.rhs, w.err);
+          g.sync();
+        } else if (lowp == 2) {
+          if (g.warp() == g.lead) low_solve<FF>(w, N, reinterpret_cast<const FF*>(w.invdiag), w.rhs, w.err);
           g.sync();
         } else {
           for (int i = g.t; i < N; i += NT) w.err[i] = w.rhs[i];
@@ -1173,10 +1224,13 @@ static int integrate_impl(const chem_mech* mc, double p_Pa, double* T, double* Y
   chem_default_opts(&o);
   if (opts) o = *opts;
   if (o.max_steps < 1) return set_err(CHEM_EINVAL, "chem_integrate: max_steps < 1");
-  if (o.precision != CHEM_PREC_FP64 && o.precision != CHEM_PREC_MIXED)
+  if (o.precision != CHEM_PREC_FP64 && o.precision != CHEM_PREC_MIXED &&
+      o.precision != CHEM_PREC_MIXED_FF)
     return set_err(CHEM_EINVAL, "chem_integrate: unknown precision mode");
   if (o.precision == CHEM_PREC_MIXED && (o.refine_sweeps < 1 || o.refine_sweeps > 4))
     return set_err(CHEM_EINVAL, "chem_integrate: refine_sweeps must be 1..4");
+  if (o.precision == CHEM_PREC_MIXED_FF && (o.refine_sweeps < 0 || o.refine_sweeps > 4))
+    return set_err(CHEM_EINVAL, "chem_integrate: refine_sweeps must be 0..4");
   if (o.solver != CHEM_SOLVER_ROSENBROCK && o.solver != CHEM_SOLVER_SEULEX)
     return set_err(CHEM_EINVAL, "chem_integrate: unknown solver");
   if (o.solver == CHEM_SOLVER_SEULEX && (o.precision != CHEM_PREC_FP64 || rec))
@@ -1216,7 +1270,8 @@ static int integrate_impl(const chem_mech* mc, double p_Pa, double* T, double* Y
   a.steps_out = m->d_steps; a.rej_out = m->d_rej;
   a.totals = m->d_totals; a.queue = m->d_queue;
   a.ncells = ncells; a.first = 0; a.count = ncells; a.max_steps = o.max_steps; a.use_queue = o.use_queue;
-  a.mixed = o.precision == CHEM_PREC_MIXED; a.refine_sweeps = o.refine_sweeps;
+  a.mixed = o.precision == CHEM_PREC_MIXED ? 1 : o.precision == CHEM_PREC_MIXED_FF ? 2 : 0;
+  a.refine_sweeps = o.refine_sweeps;
   a.rec = rec; a.rec_cap = rec_cap;
   a.solver = o.solver;
   a.fdjac = o.jacobian == CHEM_JAC_FD;
@@ -1473,10 +1528,13 @@ int chem_integrate_noalloc(const chem_mech* mc, double p_Pa, double* T, double* 
   chem_default_opts(&o);
   if (opts) o = *opts;
   if (o.max_steps < 1) return set_err(CHEM_EINVAL, "chem_integrate_noalloc: max_steps < 1");
-  if (o.precision != CHEM_PREC_FP64 && o.precision != CHEM_PREC_MIXED)
+  if (o.precision != CHEM_PREC_FP64 && o.precision != CHEM_PREC_MIXED &&
+      o.precision != CHEM_PREC_MIXED_FF)
     return set_err(CHEM_EINVAL, "chem_integrate_noalloc: unknown precision mode");
   if (o.precision == CHEM_PREC_MIXED && (o.refine_sweeps < 1 || o.refine_sweeps > 4))
     return set_err(CHEM_EINVAL, "chem_integrate_noalloc: refine_sweeps must be 1..4");
+  if (o.precision == CHEM_PREC_MIXED_FF && (o.refine_sweeps < 0 || o.refine_sweeps > 4))
+    return set_err(CHEM_EINVAL, "chem_integrate_noalloc: refine_sweeps must be 0..4");
   if (o.solver != CHEM_SOLVER_ROSENBROCK && o.solver != CHEM_SOLVER_SEULEX)
     return set_err(CHEM_EINVAL, "chem_integrate_noalloc: unknown solver");
   if (o.solver == CHEM_SOLVER_SEULEX && o.precision != CHEM_PREC_FP64)
@@ -1510,7 +1568,8 @@ int chem_integrate_noalloc(const chem_mech* mc, double p_Pa, double* T, double* 
   a.totals = reinterpret_cast<unsigned long long*>(s + 64);
   a.queue = reinterpret_cast<int*>(s);
   a.ncells = ncells; a.first = 0; a.count = ncells; a.max_steps = o.max_steps; a.use_queue = o.use_queue;
-  a.mixed = o.precision == CHEM_PREC_MIXED; a.refine_sweeps = o.refine_sweeps;
+  a.mixed = o.precision == CHEM_PREC_MIXED ? 1 : o.precision == CHEM_PREC_MIXED_FF ? 2 : 0;
+  a.refine_sweeps = o.refine_sweeps;
   a.solver = o.solver;
   a.fdjac = o.jacobian == CHEM_JAC_FD;
   launch_integrate(L, st, m->dev, a);

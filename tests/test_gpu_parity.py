@@ -210,3 +210,22 @@ def test_integrate_parity_mixed_precision(which, request):
     # an attempt whose FP32 refinement does not converge is redone with FP64 factors, and the
     # cell then stays on FP64 factors for 16 attempts: fallbacks stay a small fraction
     assert stats.refine_fallbacks <= 0.1 * (stats.steps + stats.rejects)
+
+
+@pytest.mark.parametrize("sweeps", [2, 0])
+@pytest.mark.parametrize("which", ["small", "shear"])
+def test_integrate_parity_fp32_pairs(which, sweeps, request):
+    """LU and substitutions in FP32 pairs (about 48 significand bits) match the FP64 oracle to
+    the integrate tolerance, with FP64-residual refinement (2 sweeps at most) and without it."""
+    w, mech, ora = request.getfixturevalue(which)
+    idx = np.arange(256) if which == "small" else _sample_shear(16, 3)
+    T, Y = w["T"][idx], w["Y"][:, idx]
+    opts = chem.default_opts(precision=chem.CHEM_PREC_MIXED_FF, refine_sweeps=sweeps)
+    Tg, Yg, sg, stats, steps, _ = _gpu_integrate(mech, w, T, Y, opts=opts)
+    To, Yo, so, steps_o, _ = ora.integrate(w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], nthreads=16)
+    assert np.all(sg == 0) and np.all(so == 0)
+    _assert_state_close(Tg, Yg, To, Yo)
+    # pair factors solve to ~kappa 2^-48: one sweep converges, the FP64 fallback stays rare
+    assert stats.refine_fallbacks <= 0.005 * (stats.steps + stats.rejects)
+    # the same steps as the FP64 oracle, up to a few attempts decided by rounding in err ~ 1
+    assert np.all(np.abs(steps.astype(np.int64) - steps_o) <= 0.01 * steps_o + 2)
