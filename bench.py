@@ -41,10 +41,10 @@ OPCOUNT_FILE = os.path.join(ROOT, "tests", "golden", "opcount_mech53.json")
 # (measured FP64 pipe throughput of exp and log relative to DFMA on GB300: 17 and 31 DFMA)
 FLOP_WEIGHTS = {"add": 1, "mul": 1, "div": 1, "exp": 2 * 17, "log": 2 * 31}
 # DRAM bytes (read + write) of the integrate kernel per cell, from the ncu capture summarised in
-# profiles/integrate_kernel_mech53_shear.md (608-cell slice of the shear-layer field: 1.143 MB
+# profiles/integrate_kernel_mech53_shear.md (608-cell slice of the shear-layer field: 1.387 MB
 # read, 0 B written); the kernel's DRAM traffic is the per-cell state and the tables, so it scales
 # with the cells of a launch
-TRAFFIC_BYTES_PER_CELL = 1143296 / 608
+TRAFFIC_BYTES_PER_CELL = 1386752 / 608
 
 
 def _env_int(name, default):
