@@ -19,6 +19,7 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -31,29 +32,38 @@ _SRC = os.path.join(_HERE, "chem_oracle.cpp")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libchem_oracle.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}  # compiled oracle per planted-mistake id (0 = the oracle itself)
+_plant = 0
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
 _lp = ctypes.POINTER(ctypes.c_int64)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with the host C++ compiler (portable flags only)."""
+def _lib_path(plant: int) -> str:
+    return _LIB_PATH if plant == 0 else os.path.join(_BUILD, f"libchem_oracle_plant{plant}.so")
+
+
+def build(force: bool = False, plant: int = 0) -> str:
+    """Compile the oracle with the host C++ compiler (portable flags only).  plant > 0 builds the
+    variant with that planted mistake (chem_oracle.cpp, ORACLE_PLANT; pin tests only)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    path = _lib_path(plant)
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + f".{os.getpid()}.tmp"
         cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC]
+        if plant:
+            cmd.insert(1, f"-DORACLE_PLANT={int(plant)}")
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+        os.replace(tmp, path)
+    return path
 
 
 def _load():
-    global _lib
+    plant = _plant
     with _lock:
-        if _lib is None:
-            lib = ctypes.CDLL(build())
+        if plant not in _libs:
+            lib = ctypes.CDLL(build(plant=plant))
             lib.oracle_load.restype = ctypes.c_void_p
             lib.oracle_load.argtypes = [ctypes.c_char_p]
             lib.oracle_free.argtypes = [ctypes.c_void_p]
@@ -78,8 +88,21 @@ def _load():
                                           _dp, _dp]
             lib.oracle_jacobian_fd.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp]
             lib.oracle_jacobian_dir.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
-            _lib = lib
-    return _lib
+            _libs[plant] = lib
+    return _libs[plant]
+
+
+@contextlib.contextmanager
+def planted(plant: int):
+    """Pin tests only: OracleMechanism objects and ros_coefficients() made inside the block use
+    the oracle compiled with planted mistake `plant` (chem_oracle.cpp, ORACLE_PLANT)."""
+    global _plant
+    old = _plant
+    _plant = int(plant)
+    try:
+        yield
+    finally:
+        _plant = old
 
 
 def _p(a, ptype=_dp):

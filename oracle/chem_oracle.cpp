@@ -24,6 +24,14 @@
 // count used by the benchmark's roofline).
 //
 // Units: cgs (mol, cm, s, erg), temperature in K, activation energies in cal/mol.
+//
+// Planted mistakes: compiled with -DORACLE_PLANT=n (n = 1..10) the oracle carries one
+// deliberate error, marked "plant n" below, so that tests/test_oracle_planted.py can check that
+// each of them fails at least one of the oracle's pins.  The default (0) is the oracle itself.
+
+#ifndef ORACLE_PLANT
+#define ORACLE_PLANT 0
+#endif
 
 #include <algorithm>
 #include <atomic>
@@ -524,8 +532,8 @@ static void thermo(const Mech& m, const S& T, Thermo<S>& th) {
   for (int k = 0; k < m.K; ++k) {
     const std::vector<double>& a = (re(T) <= m.Tmid[k]) ? m.alow[k] : m.ahigh[k];
     th.cp_R[k] = S(a[0]) + S(a[1]) * T + S(a[2]) * T * T + S(a[3]) * T * T * T + S(a[4]) * T * T * T * T;
-    th.h_RT[k] = S(a[0]) + S(a[1]) * T / S(2.0) + S(a[2]) * T * T / S(3.0) + S(a[3]) * T * T * T / S(4.0) +
-                 S(a[4]) * T * T * T * T / S(5.0) + S(a[5]) / T;
+    th.h_RT[k] = S(a[0]) + S(a[1]) * T / S(2.0) + S(a[2]) * T * T / S(ORACLE_PLANT == 4 ? 2.0 : 3.0) +
+                 S(a[3]) * T * T * T / S(4.0) + S(a[4]) * T * T * T * T / S(5.0) + S(a[5]) / T;  // plant 4
     th.s_R[k] = S(a[0]) * lnT + S(a[1]) * T + S(a[2]) * T * T / S(2.0) + S(a[3]) * T * T * T / S(3.0) +
                 S(a[4]) * T * T * T * T / S(4.0) + S(a[6]);
     th.dcp_RdT[k] = S(a[1]) + S(2.0) * S(a[2]) * T + S(3.0) * S(a[3]) * T * T + S(4.0) * S(a[4]) * T * T * T;
@@ -563,7 +571,7 @@ static void troe_F(const Reaction& x, const S& T, const S& Pr, S& F, S& dlog10F_
   const double a = x.troe[0], T3 = x.troe[1], T1 = x.troe[2], T2 = x.troe[3];
   S Fcent = S(1.0 - a) * exp(-T / S(T3)) + S(a) * exp(-T / S(T1)) + exp(-S(T2) / T);
   S L = log10_(Fcent);
-  S c = S(-0.4) - S(0.67) * L;
+  S c = S(-0.4) - S(ORACLE_PLANT == 7 ? -0.67 : 0.67) * L;  // plant 7
   S n = S(0.75) - S(1.27) * L;
   S x10 = log10_(Pr);
   S den = n - S(0.14) * (x10 + c);
@@ -603,7 +611,7 @@ static void rates(const Mech& m, double p, const S* phi, S* f, RateState<S>& st,
     S kf = exp(lnA + S(x.b) * lnT - S(x.Ea / kRc) * invT);
     S M = S(0.0);
     if (x.type >= 1) {
-      for (int k = 0; k < K; ++k) M += S(x.eff[k]) * st.C[k];
+      for (int k = 0; k < K; ++k) M += S(ORACLE_PLANT == 9 ? 1.0 : x.eff[k]) * st.C[k];  // plant 9
     }
     if (x.type >= 2) {
       S k0 = exp(S(std::log(x.A0)) + S(x.b0) * lnT - S(x.Ea0 / kRc) * invT);
@@ -620,7 +628,7 @@ static void rates(const Mech& m, double p, const S* phi, S* f, RateState<S>& st,
       if (x.prod[s] >= 0) { dG_RT += st.th.h_RT[x.prod[s]] - st.th.s_R[x.prod[s]]; dnu += 1; }
       if (x.reac[s] >= 0) { dG_RT -= st.th.h_RT[x.reac[s]] - st.th.s_R[x.reac[s]]; dnu -= 1; }
     }
-    S Kc = exp(-dG_RT + S((double)dnu) * ln_patm_rut);
+    S Kc = exp(-dG_RT + S((double)(ORACLE_PLANT == 1 ? -dnu : dnu)) * ln_patm_rut);  // plant 1
     S kr = kf / Kc;
     S pf = S(1.0), pr = S(1.0);
     for (int s = 0; s < 2; ++s) {
@@ -628,7 +636,7 @@ static void rates(const Mech& m, double p, const S* phi, S* f, RateState<S>& st,
       if (x.prod[s] >= 0) pr *= st.C[x.prod[s]];
     }
     S qf = kf * pf, qr = kr * pr;
-    if (x.type == 1) { qf *= M; qr *= M; }
+    if (x.type == 1) { qf *= M; if (ORACLE_PLANT != 5) qr *= M; }  // plant 5
     st.kf[r] = kf; st.kr[r] = kr; st.M[r] = M; st.qf[r] = qf; st.qr[r] = qr; st.q[r] = qf - qr;
   }
   st.omega.assign(K, S(0.0));
@@ -639,8 +647,8 @@ static void rates(const Mech& m, double p, const S* phi, S* f, RateState<S>& st,
   for (int k = 0; k < K; ++k) st.cp_mass += st.Y[k] * st.th.cp_R[k] * S(kRu) / S(m.W[k]);
   S Q = S(0.0);  // sum_k H_k omega_k, erg/(cm^3 s)
   for (int k = 0; k < K; ++k) Q += st.th.h_RT[k] * S(kRu) * st.T * st.omega[k];
-  f[0] = -Q / (st.rho * st.cp_mass);
-  for (int k = 0; k < K - 1; ++k) f[1 + k] = S(m.W[k]) * st.omega[k] / st.rho;
+  f[0] = (ORACLE_PLANT == 3 ? Q : -Q) / (st.rho * st.cp_mass);  // plant 3
+  for (int k = 0; k < K - 1; ++k) f[1 + k] = S(ORACLE_PLANT == 2 ? 1.0 : m.W[k]) * st.omega[k] / st.rho;  // plant 2
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -666,7 +674,11 @@ static void jacobian(const Mech& m, double p, const S* phi, S* f, S* J, const S*
   rates(m, p, phi, f, st, lnA_shift);
   const S T = st.T, invT = S(1.0) / T;
   std::vector<S> dlnrho_dY(K - 1);
+#if ORACLE_PLANT == 6
+  for (int i = 0; i < K - 1; ++i) dlnrho_dY[i] = st.Wbar * (S(1.0) / S(m.W[i]) - S(1.0) / S(m.W[d]));  // plant 6
+#else
   for (int i = 0; i < K - 1; ++i) dlnrho_dY[i] = -st.Wbar * (S(1.0) / S(m.W[i]) - S(1.0) / S(m.W[d]));
+#endif
   // Z = d omega / dC (K x K), and dw/dT at fixed C
   std::vector<S> Z((size_t)K * K, S(0.0)), domega_dT(K, S(0.0));
   std::vector<S> dqdC(K);
@@ -701,7 +713,7 @@ static void jacobian(const Mech& m, double p, const S* phi, S* f, S* J, const S*
       if (x.reac[s] >= 0) { dH_RT -= st.th.h_RT[x.reac[s]]; dnu -= 1; }
     }
     // d(g/RT)/dT = -(h/RT)/T  ->  d ln Kc/dT = (sum nu h/RT)/T - (sum nu)/T
-    S dlnKc_dT = (dH_RT - S((double)dnu)) * invT;
+    S dlnKc_dT = (dH_RT - S((double)(ORACLE_PLANT == 1 ? -dnu : dnu))) * invT;  // plant 1
     if (x.type == 1) {
       S R0 = st.kf[r] * pf - st.kr[r] * pr;
       for (int j = 0; j < K; ++j) dqdC[j] += S(x.eff[j]) * R0;
@@ -729,13 +741,14 @@ static void jacobian(const Mech& m, double p, const S* phi, S* f, S* J, const S*
         S dFcent_dT = -S(1.0 - a) / S(T3) * e3 - S(a) / S(T1) * e1 + S(T2) * invT * invT * e2;
         S L = log10_(Fcent);
         S dL_dT = dFcent_dT / (Fcent * S(std::log(10.0)));
-        S c = S(-0.4) - S(0.67) * L, n = S(0.75) - S(1.27) * L;
+        S c = S(-0.4) - S(ORACLE_PLANT == 7 ? -0.67 : 0.67) * L, n = S(0.75) - S(1.27) * L;  // plant 7
         S x10 = log10_(Pr);
         S den = n - S(0.14) * (x10 + c);
         S f1 = (x10 + c) / den;
         S g = S(1.0) + f1 * f1;
         // d f1 / dL at fixed Pr, with dc/dL = -0.67, dn/dL = -1.27
-        S df1_dL = (S(-0.67) * den - (x10 + c) * (S(-1.27) - S(0.14) * S(-0.67))) / (den * den);
+        const S dc_dL = S(ORACLE_PLANT == 7 ? 0.67 : -0.67);  // plant 7
+        S df1_dL = (dc_dL * den - (x10 + c) * (S(-1.27) - S(0.14) * dc_dL)) / (den * den);
         S dlog10F_dL = S(1.0) / g - L * S(2.0) * f1 / (g * g) * df1_dL;
         dlnF_dT = S(std::log(10.0)) * dlog10F_dL * dL_dT;
       }
@@ -776,9 +789,10 @@ static void jacobian(const Mech& m, double p, const S* phi, S* f, S* J, const S*
   }
   // species rows
   for (int k = 0; k < K - 1; ++k) {
-    J[(size_t)(1 + k) * N + 0] = S(m.W[k]) / st.rho * dw_dT[k] + f[1 + k] * invT;  // -f * dlnrho/dT
+    const S Wk = S(ORACLE_PLANT == 2 ? 1.0 : m.W[k]);  // plant 2
+    J[(size_t)(1 + k) * N + 0] = Wk / st.rho * dw_dT[k] + f[1 + k] * invT;  // -f * dlnrho/dT
     for (int i = 0; i < K - 1; ++i)
-      J[(size_t)(1 + k) * N + 1 + i] = S(m.W[k]) / st.rho * dw_dY[(size_t)k * (K - 1) + i] - f[1 + k] * dlnrho_dY[i];
+      J[(size_t)(1 + k) * N + 1 + i] = Wk / st.rho * dw_dY[(size_t)k * (K - 1) + i] - f[1 + k] * dlnrho_dY[i];
   }
   // temperature row
   const S rhocp = st.rho * st.cp_mass;
@@ -790,13 +804,26 @@ static void jacobian(const Mech& m, double p, const S* phi, S* f, S* J, const S*
   }
   S dcp_dT = S(0.0);
   for (int k = 0; k < K; ++k) dcp_dT += st.Y[k] * st.th.dcp_RdT[k] * S(kRu) / S(m.W[k]);
+#if ORACLE_PLANT == 3
+  J[0] = dQ_dT / rhocp - f[0] * (-invT + dcp_dT / st.cp_mass);  // plant 3
+#else
   J[0] = -dQ_dT / rhocp - f[0] * (-invT + dcp_dT / st.cp_mass);
+#endif
   for (int i = 0; i < K - 1; ++i) {
     S dQ_dYi = S(0.0);
     for (int k = 0; k < K; ++k) dQ_dYi += st.th.h_RT[k] * S(kRu) * T * dw_dY[(size_t)k * (K - 1) + i];
     S dcp_dYi = st.th.cp_R[i] * S(kRu) / S(m.W[i]) - st.th.cp_R[d] * S(kRu) / S(m.W[d]);
+#if ORACLE_PLANT == 3
+    J[1 + i] = dQ_dYi / rhocp - f[0] * (dlnrho_dY[i] + dcp_dYi / st.cp_mass);  // plant 3
+#else
     J[1 + i] = -dQ_dYi / rhocp - f[0] * (dlnrho_dY[i] + dcp_dYi / st.cp_mass);
+#endif
   }
+#if ORACLE_PLANT == 10
+  // plant 10: the Jacobian returned transposed
+  for (int i = 0; i < N; ++i)
+    for (int j = i + 1; j < N; ++j) std::swap(J[(size_t)i * N + j], J[(size_t)j * N + i]);
+#endif
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -878,7 +905,8 @@ struct Ros4 {
                       {-2.341993140193055730037, 0, 0, 0},
                       {-0.02787068958553465628054, 0.2086236229782045434317, 0, 0},
                       {-0.2474922550210316401721, -0.1907869111079863467924, -0.23, 0}};
-  double b[4] = {0.3189845243949336284427, 0.05124233729027201389922, 0.0, 0.6297731383147943576581};
+  double b[4] = {0.3189845243949336284427 + (ORACLE_PLANT == 8 ? 1e-3 : 0.0),  // plant 8
+                 0.05124233729027201389922, 0.0, 0.6297731383147943576581};
   double bhat[4] = {0.04912862293304546304649, -0.07686730508695069897692, -0.1719498044983180858675,
                     1.199688486652223321798};
 };
