@@ -99,10 +99,18 @@ typedef struct {
 /* Fill `opts` with the defaults. */
 void chem_default_opts(chem_opts* opts);
 
-/* Load a mechanism file (text format written by the synthetic generator: elements, species
- * with molar mass and NASA 7-coefficient polynomials, reversible reactions of type elementary,
- * third-body, Lindemann or Troe fall-off) and upload its tables to the current CUDA device.
- * On success *out owns the tables until chem_free_mechanism. */
+/* Load a mechanism file and upload its tables to the current CUDA device.  Two formats:
+ *   - CHEMMECH (the first non-comment line starts with that word): the text format of the
+ *     synthetic generator -- elements, species with molar mass and NASA 7-coefficient
+ *     polynomials, reversible reactions of type elementary, third-body, Lindemann or Troe
+ *     fall-off;
+ *   - anything else is read as CHEMKIN-II (ELEMENTS, SPECIES, THERMO with NASA-7 cards,
+ *     REACTIONS with unit keywords, reversible '=' / '<=>', integer coefficients, '+M' with
+ *     efficiencies, '(+M)' with LOW and TROE, DUPLICATE).  Forms the kernels do not hold are
+ *     refused with CHEM_EFILE and a message: irreversible '=>', REV, PLOG, SRI, HIGH, FORD/RORD,
+ *     specific colliders, more than two molecules on a side.
+ * The file is parsed before the GPU is touched (a malformed file gives CHEM_EFILE on any
+ * machine).  On success *out owns the tables until chem_free_mechanism. */
 int chem_load_mechanism(const char* path, chem_mech** out);
 void chem_free_mechanism(chem_mech* mech);
 
