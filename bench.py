@@ -185,7 +185,8 @@ def run_reference(args, w, world, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["name"], "cells": int(w["T"].shape[0]), "species": 53, "reactions": 325,
                        "dt_s": w["dt"], "p_atm": 40.0, "rtol": w["rtol"], "atol": w["atol"], "precision": "fp64",
-                       "solver": "rosenbrock", "start": "cold (every step from the initial field)"},
+                       "refine_sweeps": None, "solver": "rosenbrock",
+                       "start": "cold (every step from the initial field)"},
             "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores, "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
