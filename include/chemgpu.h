@@ -114,6 +114,15 @@ void chem_default_opts(chem_opts* opts);
 int chem_load_mechanism(const char* path, chem_mech** out);
 void chem_free_mechanism(chem_mech* mech);
 
+/* Parse a mechanism file on the host (no GPU needed) and write the tables the kernels would use,
+ * in file order, as text: "species K", one line per species "sp W Tmid a_low[7] a_high[7]",
+ * "reactions R", one line per reaction "rx type n_reac reac.. n_prod prod.. A b Ea/R [eff K
+ * values] [low A0 b0 Ea0/R] [troe alpha T3 T1 T2]" (species indices ascending within a side;
+ * type 0 elementary, 1 third-body, 2 Lindemann, 3 Troe; Ea/R in K; a missing Troe T2 is 1e30).
+ * *need receives the size including the terminating NUL; cap <= 0 only queries it, a smaller
+ * positive cap gives CHEM_ESIZE.  For checking the reader against an independent one. */
+int chem_describe_mechanism(const char* path, char* buf, int64_t cap, int64_t* need);
+
 /* Number of species K (= state length N) and reactions R. */
 int chem_mech_dims(const chem_mech* mech, int* K, int* R);
 

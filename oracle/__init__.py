@@ -87,6 +87,7 @@ def _load():
             lib.oracle_replay.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, ctypes.c_int, _dp, _dp, _dp,
                                           _dp, _dp]
             lib.oracle_jacobian_fd.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp]
+            lib.oracle_describe.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int64, _lp]
             lib.oracle_jacobian_dir.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
             _libs[plant] = lib
     return _libs[plant]
@@ -132,6 +133,15 @@ class OracleMechanism:
         if h:
             self._lib.oracle_free(h)
             self._h = None
+
+    def describe(self) -> str:
+        """The oracle's reading of the mechanism file, in the text form of the library's
+        chem_describe_mechanism (for comparing the two readers)."""
+        need = ctypes.c_int64()
+        self._lib.oracle_describe(self._h, None, 0, ctypes.byref(need))
+        buf = ctypes.create_string_buffer(need.value)
+        self._lib.oracle_describe(self._h, buf, need.value, ctypes.byref(need))
+        return buf.value.decode()
 
     def thermo(self, T: float):
         out = [np.zeros(self.K) for _ in range(3)]

@@ -1245,6 +1245,49 @@ void* oracle_load(const char* path) {
 
 void oracle_free(void* h) { delete static_cast<Mech*>(h); }
 
+// The oracle's reading of the mechanism, in the text form of the library's
+// chem_describe_mechanism (species "sp W Tmid a_low a_high", reactions "rx type n_reac reac..
+// n_prod prod.. A b Ea/R [eff ..] [low A0 b0 Ea0/R] [troe alpha T3 T1 T2]"), so that tests can
+// compare the two independent readers.  *need = size with the NUL; cap <= 0 only queries it.
+int oracle_describe(void* h, char* buf, int64_t cap, int64_t* need) {
+  const Mech* m = static_cast<const Mech*>(h);
+  std::ostringstream o;
+  o.precision(17);
+  o << "species " << m->K << "\n";
+  for (int k = 0; k < m->K; ++k) {
+    o << "sp " << m->W[k] << " " << m->Tmid[k];
+    for (double a : m->alow[k]) o << " " << a;
+    for (double a : m->ahigh[k]) o << " " << a;
+    o << "\n";
+  }
+  o << "reactions " << m->R << "\n";
+  for (const Reaction& x : m->rx) {
+    o << "rx " << x.type;
+    for (const int* side : {x.reac, x.prod}) {
+      std::vector<int> sp;
+      for (int i = 0; i < 2; ++i)
+        if (side[i] >= 0) sp.push_back(side[i]);
+      std::sort(sp.begin(), sp.end());
+      o << " " << sp.size();
+      for (int k : sp) o << " " << k;
+    }
+    o << " " << x.A << " " << x.b << " " << x.Ea / kRc;
+    if (x.type >= 1) {
+      o << " eff";
+      for (double e : x.eff) o << " " << e;
+    }
+    if (x.type >= 2) o << " low " << x.A0 << " " << x.b0 << " " << x.Ea0 / kRc;
+    if (x.type == 3) o << " troe " << x.troe[0] << " " << x.troe[1] << " " << x.troe[2] << " " << x.troe[3];
+    o << "\n";
+  }
+  const std::string t = o.str();
+  *need = (int64_t)t.size() + 1;
+  if (cap <= 0) return 0;
+  if (cap < *need) return 1;
+  std::memcpy(buf, t.c_str(), t.size() + 1);
+  return 0;
+}
+
 int oracle_dims(void* h, int* K, int* R) {
   Mech* m = static_cast<Mech*>(h);
   *K = m->K; *R = m->R;

@@ -5,7 +5,8 @@ thin Python binding, `autograd` wraps the discrete adjoint in a torch.autograd.F
 holds the multi-process helpers, `autotune` picks launch shapes, and `synth` draws the seeded
 synthetic inputs.
 """
-from .chem import (ChemError, ChemOpts, ChemStats, Mechanism, chem_adjoint, chem_get_lnA,  # noqa: F401
+from .chem import (ChemError, ChemOpts, ChemStats, Mechanism, chem_adjoint, chem_describe_mechanism,  # noqa: F401
+                   chem_get_lnA,
                    chem_integrate, chem_integrate_mapped, chem_integrate_noalloc, chem_integrate_record,
                    chem_integrate_varp, chem_jacobian, chem_last_cell_counters, chem_load_mechanism, chem_rates,
                    chem_set_lnA, default_opts, load_library)

@@ -66,6 +66,7 @@ def load_library(build_if_missing: bool = True):
         lib.chem_default_opts.argtypes = [ctypes.POINTER(ChemOpts)]
         lib.chem_load_mechanism.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp)]
         lib.chem_free_mechanism.argtypes = [vp]
+        lib.chem_describe_mechanism.argtypes = [ctypes.c_char_p, ctypes.c_char_p, i64, ctypes.POINTER(i64)]
         lib.chem_mech_dims.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip)]
         lib.chem_rates.argtypes = [vp, dp, vp, vp, i64, vp, vp]
         lib.chem_jacobian.argtypes = [vp, dp, vp, vp, i64, vp, vp]
@@ -177,6 +178,17 @@ def _cells(mech, T, Y):
     if tuple(Y.shape) != (mech.K, n):
         raise ValueError(f"Y must have shape (K={mech.K}, ncells={n}), got {tuple(Y.shape)}")
     return n
+
+
+def chem_describe_mechanism(path: str) -> str:
+    """The library's reading of a mechanism file (host only, no GPU): its tables in file order as
+    text, the format of include/chemgpu.h's chem_describe_mechanism."""
+    lib = load_library()
+    need = ctypes.c_int64()
+    _check(lib.chem_describe_mechanism(path.encode(), None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(need.value)
+    _check(lib.chem_describe_mechanism(path.encode(), buf, need.value, ctypes.byref(need)))
+    return buf.value.decode()
 
 
 def chem_rates(mech: Mechanism, p_Pa: float, T, Y, out, stream=None):

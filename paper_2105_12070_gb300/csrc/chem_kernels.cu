@@ -1007,6 +1007,74 @@ void chem_default_opts(chem_opts* o) {
   o->jacobian = CHEM_JAC_ANALYTIC;
 }
 
+// The tables of a parsed mechanism in file order, as text (see chem_describe_mechanism).
+static std::string describe_tables(const HostMech& h) {
+  std::string s;
+  char num[40];
+  auto put = [&](double v) {
+    snprintf(num, sizeof num, " %.17g", v);
+    s += num;
+  };
+  s += "species " + std::to_string(h.K) + "\n";
+  for (int k = 0; k < h.K; ++k) {
+    const double* sp = &h.sp[(size_t)k * kSpDoubles];
+    s += "sp";
+    put(sp[0]);
+    for (int i = 2; i < kSpDoubles; ++i) put(sp[i]);  // Tmid, low a1..a7, high a1..a7
+    s += "\n";
+  }
+  s += "reactions " + std::to_string(h.R) + "\n";
+  std::vector<int> dev_of(h.R);
+  for (int dr = 0; dr < h.R; ++dr) dev_of[h.order[dr]] = dr;
+  for (int r = 0; r < h.R; ++r) {
+    const int dr = dev_of[r];
+    const int* ii = &h.rxi[(size_t)dr * kRxInts];
+    const double* d = &h.rxd[(size_t)dr * kRxDoubles];
+    const double* q = dr < h.n_fo ? &h.fo[(size_t)dr * kFoDoubles] : nullptr;
+    const int type = q ? (q[7] != 0.0 ? kTroe : kLindemann) : (dr < h.n_fo + h.n_tb ? kThirdBody : kElementary);
+    s += "rx " + std::to_string(type);
+    for (int side = 0; side < 2; ++side) {
+      int a = ii[2 * side], b = ii[2 * side + 1];
+      if (a > b) std::swap(a, b);
+      s += " " + std::to_string((a >= 0) + (b >= 0));
+      if (a >= 0) s += " " + std::to_string(a);
+      if (b >= 0) s += " " + std::to_string(b);
+    }
+    put(std::exp(d[0]));
+    put(d[1]);
+    put(d[2]);
+    if (type >= kThirdBody) {
+      s += " eff";
+      for (int k = 0; k < h.K; ++k) put(h.eff[(size_t)dr * h.K + k]);
+    }
+    if (q) {
+      s += " low";
+      put(std::exp(q[0]));
+      put(q[1]);
+      put(q[2]);
+      if (type == kTroe) {
+        s += " troe";
+        for (int i = 3; i < 7; ++i) put(q[i]);
+      }
+    }
+    s += "\n";
+  }
+  return s;
+}
+
+int chem_describe_mechanism(const char* path, char* buf, int64_t cap, int64_t* need) {
+  if (!path || !need || (cap > 0 && !buf)) return set_err(CHEM_EINVAL, "chem_describe_mechanism: NULL argument");
+  HostMech h;
+  std::string err;
+  if (!parse_mechanism(path, h, err)) return set_err(CHEM_EFILE, err);
+  const std::string s = describe_tables(h);
+  *need = (int64_t)s.size() + 1;
+  if (cap <= 0) return CHEM_OK;
+  if (cap < *need) return set_err(CHEM_ESIZE, "chem_describe_mechanism: buffer too small");
+  std::memcpy(buf, s.c_str(), s.size() + 1);
+  return CHEM_OK;
+}
+
 int chem_load_mechanism(const char* path, chem_mech** out) {
   if (!path || !out) return set_err(CHEM_EINVAL, "chem_load_mechanism: NULL argument");
   *out = nullptr;
