@@ -106,9 +106,10 @@ void chem_default_opts(chem_opts* opts);
  *     fall-off;
  *   - anything else is read as CHEMKIN-II (ELEMENTS, SPECIES, THERMO with NASA-7 cards,
  *     REACTIONS with unit keywords, reversible '=' / '<=>', integer coefficients, '+M' with
- *     efficiencies, '(+M)' with LOW and TROE, DUPLICATE).  Forms the kernels do not hold are
- *     refused with CHEM_EFILE and a message: irreversible '=>', REV, PLOG, SRI, HIGH, FORD/RORD,
- *     specific colliders, more than two molecules on a side.
+ *     efficiencies, '(+M)' with LOW and TROE, a named third body '(+AR)' (efficiency 1 for it,
+ *     0 for the others), DUPLICATE).  Forms the kernels do not hold are refused with
+ *     CHEM_EFILE and a message: irreversible '=>', REV, PLOG, SRI, HIGH, FORD/RORD, more than
+ *     two molecules on a side.
  * The file is parsed before the GPU is touched (a malformed file gives CHEM_EFILE on any
  * machine).  On success *out owns the tables until chem_free_mechanism. */
 int chem_load_mechanism(const char* path, chem_mech** out);

@@ -67,6 +67,7 @@ struct Reaction {
   double A0 = 0, b0 = 0, Ea0 = 0;   // low-pressure limit (fall-off)
   double troe[4] = {0, 0, 0, 0};    // alpha, T3, T1, T2
   std::vector<double> eff;          // collision efficiencies, K entries (types 1-3)
+  int collider = -1;                // CHEMKIN '(+NAME)': the species that is the third body
 };
 
 struct Mech {
@@ -284,17 +285,25 @@ static bool load_chemkin(const char* path, Mech& m, std::string& err) {
             lhs = eq.substr(0, eq.find('='));
             rhs = eq.substr(eq.find('=') + 1);
           }
-          int kind[2] = {0, 0};  // 1: +M, 2: (+M)
+          int kind[2] = {0, 0};  // 1: +M, 2: (+M) or (+NAME)
+          int named[2] = {-1, -1};
           std::vector<int> mols[2];
           std::string sides[2] = {lhs, rhs};
           for (int sd = 0; sd < 2; ++sd) {
             std::string sv = sides[sd];
-            if (sv.size() >= 4 && sv.substr(sv.size() - 4) == "(+M)") {
+            const size_t open = sv.find("(+");
+            if (open != std::string::npos) {
+              // fall-off: '(+M)' at the end of the side, or '(+NAME)' for one species as the
+              // third body (CHEMKIN convention: efficiency 1 for it, 0 for every other species)
+              if (sv.back() != ')') { err = "bad third body in " + eq; return false; }
+              const std::string who = sv.substr(open + 2, sv.size() - open - 3);
+              if (who != "M") {
+                auto it = idx.find(who);
+                if (it == idx.end()) { err = "unknown third body " + who; return false; }
+                named[sd] = it->second;
+              }
               kind[sd] = 2;
-              sv.erase(sv.size() - 4);
-            } else if (sv.find("(+") != std::string::npos) {
-              err = "specific collider not supported: " + eq;
-              return false;
+              sv.erase(open);
             }
             std::stringstream ts(sv);
             for (std::string term; std::getline(ts, term, '+');) {
@@ -309,13 +318,17 @@ static bool load_chemkin(const char* path, Mech& m, std::string& err) {
               while (coef-- > 0) mols[sd].push_back(it->second);
             }
           }
-          if (kind[0] != kind[1]) { err = "unbalanced third body in " + eq; return false; }
+          if (kind[0] != kind[1] || named[0] != named[1]) { err = "unbalanced third body in " + eq; return false; }
           for (int sd = 0; sd < 2; ++sd)
             if (mols[sd].empty() || mols[sd].size() > 2) { err = "one or two molecules per side: " + eq; return false; }
           x.reac[0] = mols[0][0]; x.reac[1] = mols[0].size() == 2 ? mols[0][1] : -1;
           x.prod[0] = mols[1][0]; x.prod[1] = mols[1].size() == 2 ? mols[1][1] : -1;
           x.type = kind[0] == 2 ? 2 : kind[0];
-          if (x.type >= 1) x.eff.assign(m.K, 1.0);
+          x.collider = named[0];
+          if (x.type >= 1) {
+            x.eff.assign(m.K, x.collider >= 0 ? 0.0 : 1.0);
+            if (x.collider >= 0) x.eff[x.collider] = 1.0;
+          }
           m.rx.push_back(x);
           continue;
         }
@@ -352,6 +365,7 @@ static bool load_chemkin(const char* path, Mech& m, std::string& err) {
           return false;
         } else {
           if (x.type < 1) { err = "efficiencies without a third body: " + l; return false; }
+          if (x.collider >= 0) { err = "efficiencies with a named third body: " + l; return false; }
           // NAME/value/ pairs
           std::string rest = l;
           while (!ck_strip(rest).empty()) {

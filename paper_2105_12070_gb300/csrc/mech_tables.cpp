@@ -64,6 +64,7 @@ struct Reader {
 
 struct FileReaction {
   int type = 0, reac[2] = {-1, -1}, prod[2] = {-1, -1};
+  int collider = -1;  // CHEMKIN '(+NAME)': the one species that acts as the third body
   double A = 0, b = 0, Ea = 0, A0 = 0, b0 = 0, Ea0 = 0, troe[4] = {0, 0, 0, 0};
   std::vector<double> eff;
 };
@@ -335,7 +336,8 @@ bool build_tables(const char* path, HostMech& m, std::vector<FileReaction>& rx, 
 //     DUPLICATE is accepted.  E units: CAL/MOLE (default), KCAL/MOLE, JOULES/MOLE, KJOULES/MOLE,
 //     KELVINS; A in mol, cm, s.
 //   Not supported (a clear error): irreversible '=>', explicit REV, PLOG, SRI, chemically
-//   activated HIGH, specific colliders (+AR), more than two molecules on a side.
+//   activated HIGH, more than two molecules on a side.  A named third body '(+AR)' makes the
+//   collision efficiency 1 for that species and 0 for the others.
 
 std::string upper(std::string s) {
   for (char& c : s) c = (char)std::toupper((unsigned char)c);
@@ -549,12 +551,21 @@ bool read_chemkin(const char* path, HostMech& m, std::vector<FileReaction>& rx, 
           else return fail("no '=' in reaction: " + eq);
           std::string side[2] = {ueq.substr(0, sep), ueq.substr(sep + seplen)};
           bool falloff[2] = {false, false}, third[2] = {false, false};
+          int collider[2] = {-1, -1};
           std::vector<int> mol[2];
           for (int sd = 0; sd < 2; ++sd) {
             std::string& sv = side[sd];
             const size_t fp = sv.find("(+");
             if (fp != std::string::npos) {
-              if (sv.substr(fp) != "(+M)") return fail("specific collider not supported: " + eq);
+              // '(+M)', or '(+NAME)': that species alone is the third body of the fall-off
+              const std::string c = sv.substr(fp + 2);
+              if (c.size() < 2 || c.back() != ')') return fail("bad third body in " + eq);
+              const std::string name = c.substr(0, c.size() - 1);
+              if (name != "M") {
+                auto it = sp_index.find(name);
+                if (it == sp_index.end()) return fail("unknown third body " + name + " in " + eq);
+                collider[sd] = it->second;
+              }
               falloff[sd] = true;
               sv = sv.substr(0, fp);
             }
@@ -575,12 +586,15 @@ bool read_chemkin(const char* path, HostMech& m, std::vector<FileReaction>& rx, 
           }
           if (falloff[0] != falloff[1] || third[0] != third[1]) return fail("unbalanced +M in " + eq);
           if (falloff[0] && third[0]) return fail("both +M and (+M) in " + eq);
+          if (collider[0] != collider[1]) return fail("different third bodies on the two sides of " + eq);
           for (int sd = 0; sd < 2; ++sd)
             if (mol[sd].empty() || mol[sd].size() > 2) return fail("one or two molecules per side only: " + eq);
           x.reac[0] = mol[0][0]; x.reac[1] = mol[0].size() > 1 ? mol[0][1] : -1;
           x.prod[0] = mol[1][0]; x.prod[1] = mol[1].size() > 1 ? mol[1][1] : -1;
           x.type = falloff[0] ? kLindemann : (third[0] ? kThirdBody : kElementary);
-          if (x.type >= kThirdBody) x.eff.assign(K, 1.0);
+          x.collider = collider[0];
+          if (x.type >= kThirdBody) x.eff.assign(K, x.collider >= 0 ? 0.0 : 1.0);
+          if (x.collider >= 0) x.eff[x.collider] = 1.0;
           rx.push_back(x);
           continue;
         }
@@ -623,6 +637,7 @@ bool read_chemkin(const char* path, HostMech& m, std::vector<FileReaction>& rx, 
           return fail("unsupported reaction keyword " + kw);
         // efficiencies: NAME/value/ NAME/value/ ...
         if (x.type == kElementary) return fail("efficiencies for a reaction without +M: " + l);
+        if (x.collider >= 0) return fail("efficiencies for a reaction with a named third body: " + l);
         size_t p = 0;
         while (p < l.size()) {
           while (p < l.size() && (l[p] == ' ' || l[p] == '\t')) ++p;

@@ -7,8 +7,9 @@ reader (each its own code) against the generator's CHEMMECH format describing th
 * a hand-written CHEMKIN file exercising KCAL/MOLE, a '2X' coefficient, '=' and '<=>', +M with a
   partial efficiency list (others 1), (+M) with LOW and a three-parameter TROE (no T2 term),
   DUPLICATE and '!' comments equals its CHEMMECH transcription;
-* unsupported forms (irreversible '=>', three molecules on a side, PLOG, a specific collider,
-  unknown species) are refused by both readers with a message;
+* a named third body '(+D)' equals the transcription with efficiency 1 for D and 0 elsewhere;
+* unsupported forms (irreversible '=>', three molecules on a side, PLOG, efficiencies after a
+  named third body, unknown species) are refused by both readers with a message;
 * the library's reader (CPU: chem_load_mechanism parses before it touches the GPU) accepts the
   valid files and refuses the invalid ones with CHEM_EFILE.  GPU rates and integration from
   CHEMKIN files are compared with the oracle in tests/test_gpu_chemkin.py.
@@ -125,11 +126,31 @@ def test_hand_written_chemkin_equals_its_transcription():
         np.abs(om.jacobian(1e5, T, Y)))
 
 
+def test_named_third_body_equals_one_hot_efficiencies():
+    # (+D): a Lindemann fall-off whose third body is D alone
+    ck = _toy_chemkin("A+B(+D)<=>C(+D)  5.0E11  0.2  4.0\nLOW / 2.0E15 -0.3 1.5 /")
+    cm = _toy_chemmech().replace("reactions 5", "reactions 6").replace(
+        "end", "2 2 0 1 1 2 -1 5e11 0.2 4000.0\neff 0.0 0.0 0.0 1.0\nlow 2e15 -0.3 1500.0\nend")
+    oc = O.OracleMechanism(_write(ck, ".ck"))
+    om = O.OracleMechanism(_write(cm, ".txt"))
+    rng = np.random.default_rng(4)
+    T = rng.uniform(800.0, 2000.0, size=16)
+    Y = rng.dirichlet(np.ones(4), size=16).T.copy()
+    for p in (1e5, 4e6):
+        fc, gc = oc.rates(p, T, Y, gross=True)
+        fm, gm = om.rates(p, T, Y, gross=True)
+        assert np.max(np.abs(fc - fm) / gm) <= 1e-13
+    # the library reads the same tables (checked in full by tests/test_chemkin_readers.py)
+    lines = chem.chem_describe_mechanism(_write(ck, ".ck")).splitlines()
+    assert lines[-1].startswith("rx 2 2 0 1 1 2 ") and " eff 0 0 0 1 low " in lines[-1]
+
+
 BAD = {
     "irreversible": "A+B=>C 1.0E12 0.0 1.0",
     "three molecules": "A+A+B<=>C+B 1.0E12 0.0 1.0",
     "plog": "A<=>B 1.0E12 0.0 1.0\nPLOG / 1.0 1.0E12 0.0 1.0 /",
-    "specific collider": "A+B(+D)<=>C(+D) 1.0E12 0.0 1.0\nLOW / 1.0E16 0.0 1.0 /",
+    "efficiencies after a named third body": "A+B(+D)<=>C(+D) 1.0E12 0.0 1.0\nLOW / 1.0E16 0.0 1.0 /\nC/2.0/",
+    "two different named third bodies": "A+B(+D)<=>C(+A) 1.0E12 0.0 1.0\nLOW / 1.0E16 0.0 1.0 /",
     "unknown species": "A+Q<=>C 1.0E12 0.0 1.0",
 }
 

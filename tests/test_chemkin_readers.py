@@ -5,7 +5,8 @@ describe): species molar mass, T_mid and NASA coefficients; per reaction the kin
 of each side, A, b, Ea/R, efficiencies, the low-pressure limit and the Troe parameters.  For the
 generator's CHEMMECH files and for CHEMKIN-II files in the syntax variants real files use (unit
 keywords, lower case and four-letter keywords, species names with parentheses, Troe with and
-without T2, per-species T_mid, efficiency lists over two lines, comments and blank lines) the
+without T2, a named third body, per-species T_mid, efficiency lists over two lines, comments and
+blank lines) the
 two readings must agree to rounding, or both readers must refuse the file.
 """
 import os
@@ -117,6 +118,8 @@ _REACTIONS = [
     "TROE / 0.45 100.0 1500.0 5000.0 /",
     "B+D(+M)<=>C+D(+M)  2.0E11  0.0  7.0",
     "LOW / 5.0E15 -1.0 0.0 /",
+    "A+B(+D)<=>C(+D)  5.0E11  0.2  4.0   ! D alone is the third body",
+    "LOW / 2.0E15 -0.3 1.5 /",
 ]
 
 
