@@ -209,3 +209,27 @@ def test_describe_refuses_bad_files():
     assert lib.chem_describe_mechanism(path.encode(), None, 0, ctypes.byref(n)) == 0 and n.value > 100
     buf = ctypes.create_string_buffer(8)
     assert lib.chem_describe_mechanism(path.encode(), buf, 8, ctypes.byref(n)) == -4
+
+
+def _thermo_variants():
+    base = _variant()
+    el, lo, hi = _TOY_THERMO["A"]
+    extra = "\n".join(_nasa_card("EXTRA", el, lo, hi))
+    i = base.index("\nEND\nREACTIONS")
+    j = base.index("   300.000  1000.000  5000.000")
+    k = base.index("D                 TOY")
+    return {
+        "THERMO without ALL": (base.replace("THERMO ALL", "THERMO"), True),
+        "a thermo card for a species not in SPECIES": (base[:i] + "\n" + extra + base[i:], True),
+        "a comment line in THERMO": (base[:j] + "! thermo comment\n" + base[j:], True),
+        "a species without thermo": (base[:k] + base[k:].split("\n", 4)[4], False),
+    }
+
+
+@pytest.mark.parametrize("case", sorted(_thermo_variants()))
+def test_thermo_section_variants(case):
+    text, valid = _thermo_variants()[case]
+    lib, ora = _both(_write(text))
+    assert (lib is not None) == valid and (ora is not None) == valid, case
+    if valid:
+        _compare(lib, ora)
