@@ -2,8 +2,8 @@
 
 The compute path is the CUDA library libchemgpu.so (C ABI in include/chemgpu.h); `chem` is its
 thin Python binding, `autograd` wraps the discrete adjoint in a torch.autograd.Function, `ranks`
-holds the multi-process helpers, `autotune` picks launch shapes, and `synth` draws the seeded
-synthetic inputs.
+holds the multi-process helpers, `autotune` picks launch shapes, `phases` prints the kernel's
+per-phase cycle counters, and `synth` draws the seeded synthetic inputs.
 """
 from .chem import (ChemError, ChemOpts, ChemStats, Mechanism, chem_adjoint, chem_describe_mechanism,  # noqa: F401
                    chem_get_lnA,
