@@ -16,6 +16,11 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   replay / TLM -- replay of the recorded steps equals the adaptive run bit for bit; the dual-number
                   tangent-linear result equals central differences of the replay (state and ln A
                   directions) and the ln k / initial-state derivatives of the Bateman solution
+  readers      -- CHEMMECH and CHEMKIN-II readings equal each other and the library's own reader
+                  (describe), on the synthetic mechanisms and CHEMKIN syntax variants
+
+`planted(n)` switches to a build with planted mistake n (tests/test_oracle_planted.py shows that
+each one fails the pin that guards it).
 """
 from __future__ import annotations
 
