@@ -2,14 +2,22 @@
 
 Workload (one "step"): one chem_integrate call over dt = 1e-5 s for the 256 x 256 (65 536
 cells) shear-layer field of the 53-species / 325-reaction synthetic mechanism at 40 atm,
-rtol 1e-6, atol 1e-10, cold start (every step starts from the same initial field).
+rtol 1e-6, atol 1e-10, cold start (every step starts from the same initial field, copied in
+outside the timed region).
 
 Reported: `value` = cells / (device time of the integrate call, CUDA events on the launching
-stream) with the field resident in HBM; `e2e` = the same cells / (H2D copy of the field from
-pinned host memory + the call + D2H copy of the result); `roofline` = achieved FP64 FLOP/s of the
-integrate kernel (algorithmic FLOPs from the oracle's per-step operation count, times the
-kernel's own per-cell step counts) against the FP64 pipe peak; `cpu_baseline` = the CPU oracle
-on a bounded sample of the same field on the host cores.
+stream) with the field resident in HBM; `e2e` = the same cells / (wall time of one
+chem_integrate call through the C ABI with pinned HOST arrays: the library copies the field in,
+integrates and copies it back inside the call); `roofline` = achieved FP64 FLOP/s of the integrate
+kernel (algorithmic FLOPs from the oracle's per-step operation count, times the kernel's own
+per-cell step counts) against the FP64 pipe peak; `cpu_baseline` = the CPU oracle on a bounded
+sample of the same field on the host cores, and on one core.
+
+Warm-up calls run on a slice of the field (one wave of cells, the same options and launch path);
+one more untimed full-size call with a one-attempt step cap allocates the library's per-cell and
+staging buffers before the timed region.  A wall-time budget (`--budget-s`) stops the timed loop
+early, and says so in the line (`steps` < `steps_requested`), if the remaining steps cannot finish
+in time.
 
 `--impl reference` times the CPU oracle itself (the reference implementation of this repo's
 method) on a bounded sample per step.
@@ -31,20 +39,24 @@ import time
 
 import numpy as np
 
+T_START = time.monotonic()
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cells/s per CFD Δt (53 sp, rtol 1e-6), batched/mixed vs plain FP64; % roofline"
 L2_BYTES = 129 * 2 ** 20
 OPCOUNT_FILE = os.path.join(ROOT, "tests", "golden", "opcount_mech53.json")
-# FLOPs per operation: add, mul and div count 1; an exp or log counts its cost in FMA flops
-# (measured FP64 pipe throughput of exp and log relative to DFMA on GB300: 17 and 31 DFMA)
+# FLOPs per operation.  Unit weights: add, mul, div, exp and log count one each (the conservative
+# count, `roofline.frac`).  Weighted: an exp or log counts its cost in FMA flops, the measured FP64
+# pipe throughput of the library exp and log relative to DFMA on GB300 (17 and 31 DFMA),
+# reported beside it as `roofline.frac_weighted`.
+UNIT_WEIGHTS = {"add": 1, "mul": 1, "div": 1, "exp": 1, "log": 1}
 FLOP_WEIGHTS = {"add": 1, "mul": 1, "div": 1, "exp": 2 * 17, "log": 2 * 31}
-# DRAM bytes (read + write) of the integrate kernel per cell, from the ncu capture summarised in
-# profiles/integrate_kernel_mech53_shear.md (608-cell slice of the shear-layer field: 1.387 MB
-# read, 0 B written); the kernel's DRAM traffic is the per-cell state and the tables, so it scales
-# with the cells of a launch
-TRAFFIC_BYTES_PER_CELL = 1386752 / 608
+# DRAM bytes (read + write) of the integrate kernel as a function of the cells of a launch,
+# fitted to two ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernel
+# on evenly spaced slices of the shear-layer field: fixed bytes (mechanism tables, launch) plus
+# bytes per cell (its state).  None until both captures have been taken on the current kernel.
+TRAFFIC_FIT = None  # {"fixed": bytes, "per_cell": bytes, "cells": (n1, n2)}
 
 
 def _env_int(name, default):
@@ -54,18 +66,23 @@ def _env_int(name, default):
         return default
 
 
-def parse_args():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--precision", choices=["fp64", "mixed", "ff"], default="fp64",
                     help="linear solves: FP64, FP32 LU + FP64 refinement, or FP32-pair LU + FP64 refinement")
     ap.add_argument("--refine-sweeps", type=int, default=-1, help="refinement sweeps per stage solve (mixed, ff)")
     ap.add_argument("--solver", choices=["rosenbrock", "seulex"], default="rosenbrock",
-                    help="integrator: the 4-stage Rosenbrock method or the paper's Seulex")
-    ap.add_argument("--cells", type=int, default=0, help="cells per rank (0 = the full 65536-cell field)")
+                    help="integrator: the Rosenbrock method or the paper's Seulex")
+    ap.add_argument("--cells", type=int, default=0, help="cells per rank (0 = the full field of the workload)")
+    ap.add_argument("--warm-cells", type=int, default=608,
+                    help="cells of each warm-up call (a slice of the field; 608 = 4 cells on each of 152 SMs)")
+    ap.add_argument("--budget-s", type=float, default=1500.0,
+                    help="wall-time budget of the whole run in seconds (the timed loop stops early if the rest "
+                         "cannot finish inside it)")
     ap.add_argument("--dt", type=float, default=0.0, help="override the CFD time step (profiling small cases)")
     ap.add_argument("--workload", choices=["shear", "uneven", "adjoint", "0d"], default="shear",
                     help="shear: 53-species shear layer (the headline); uneven: 100-species igniting/cold/burnt field")
@@ -74,6 +91,7 @@ def parse_args():
                     help="also time one launch per batch of this many cells (static assignment) against the queue")
     ap.add_argument("--autotune", action="store_true", help="pick warps/cell and cells/CTA with the autotuner first")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer call (profiling runs)")
     ap.add_argument("--rtol", type=float, default=0.0, help="override the workload's rtol (work-precision runs)")
     ap.add_argument("--accuracy-sample", type=int, default=0,
                     help="error of the timed result on this many evenly spaced cells against a converged FP64 "
@@ -86,8 +104,8 @@ def parse_args():
                          "the speed ratio and the largest deviation of T and Y from it")
     ap.add_argument("--warm-start", action="store_true",
                     help="also time the next CFD step: from the state at dt, with the carried-over sub-step h")
-    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0 = auto)")
-    return ap.parse_args()
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle's all-core sample")
+    return ap.parse_args(argv)
 
 
 class ClockSampler:
@@ -150,57 +168,96 @@ def dist_setup(args):
     return world, rank, local
 
 
-def cpu_baseline(w, n_sample: int):
-    """The CPU oracle on a bounded sample of the field, all host cores (threads over cells)."""
-    import oracle
-    cores = os.cpu_count() or 1
-    path = w["mech"].write_temp()
-    ora = oracle.OracleMechanism(path)
-    n = w["T"].shape[0]
-    idx = np.linspace(0, n - 1, n_sample).astype(np.int64)
+# ------------------------------------------------------------------------------------------------
+# CPU legs: the oracle (plain FP64 C++, one cell per thread at a time) on bounded samples
+
+def _oracle_seconds(ora, w, idx, nthreads):
     T, Y = w["T"][idx], w["Y"][:, idx]
     t0 = time.perf_counter()
-    ora.integrate(w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], nthreads=cores)
-    dt = time.perf_counter() - t0
-    return {"value": n_sample / dt, "unit": "cells/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n_sample} cells evenly spaced over the same 65536-cell field, one integrate each, "
-                      f"{cores} threads (one cell per thread at a time)", "seconds": dt}
+    ora.integrate(w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], nthreads=nthreads)
+    return time.perf_counter() - t0
+
+
+def sample_sizes(rate_all: float, cores: int, target_s: float, n_field: int):
+    """All-core sample of about target_s seconds (a multiple of the core count, at least one cell
+    per core, at most the field) and a single-core sample of about target_s / 2 seconds
+    (2..64 cells), from a measured all-core rate in cells/s."""
+    n_all = int(rate_all * target_s) // cores * cores
+    n_all = max(cores, min(n_all, n_field))
+    n_one = int(rate_all / cores * target_s / 2)
+    n_one = max(2, min(n_one, 64, n_field))
+    return n_all, n_one
+
+
+def cpu_baseline(w, target_s: float = 15.0):
+    """The CPU oracle on bounded, evenly spaced samples of the field: all host cores (threads over
+    cells), and one core (labelled; the rate of a single-threaded solve)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    ora = oracle.OracleMechanism(w["mech"].write_temp())
+    n = w["T"].shape[0]
+    probe = np.linspace(0, n - 1, cores).astype(np.int64)
+    rate0 = cores / _oracle_seconds(ora, w, probe, cores)
+    n_all, n_one = sample_sizes(rate0, cores, target_s, n)
+    idx = np.linspace(0, n - 1, n_all).astype(np.int64)
+    s_all = _oracle_seconds(ora, w, idx, cores)
+    idx1 = np.linspace(0, n - 1, n_one).astype(np.int64)
+    s_one = _oracle_seconds(ora, w, idx1, 1)
+    return {"value": n_all / s_all, "unit": "cells/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_all} cells evenly spaced over the same {n}-cell field, one integrate each, "
+                      f"{cores} threads (one cell per thread at a time)", "seconds": s_all,
+            "single_core": {"value": n_one / s_one, "unit": "cells/s", "cores": 1, "cells": n_one,
+                            "seconds": s_one,
+                            "sample": f"{n_one} cells evenly spaced over the field, one thread"}}
 
 
 def run_reference(args, w, world, rank):
+    """The oracle as the reference arm: each step a bounded sample of the workload on all host
+    cores (rank 0 only; other ranks exit without work)."""
     if rank != 0:
         return 0
+    import oracle
     cores = os.cpu_count() or 1
-    n_sample = args.cpu_sample or max(cores * 4, 32)
-    for _ in range(args.warmup):
-        cpu_baseline(w, max(cores, 8))
-    vals = []
+    ora = oracle.OracleMechanism(w["mech"].write_temp())
+    n = w["T"].shape[0]
+    probe = np.linspace(0, n - 1, cores).astype(np.int64)
+    for _ in range(max(0, args.warmup)):
+        rate0 = cores / _oracle_seconds(ora, w, probe, cores)
+    if args.warmup <= 0:
+        rate0 = cores / _oracle_seconds(ora, w, probe, cores)
+    # about 120 s of timed CPU work in total, at least one cell per core per step
+    per_step = max(cores, int(rate0 * 120.0 / max(1, args.steps)) // cores * cores)
+    per_step = min(per_step, n)
+    idx = np.linspace(0, n - 1, per_step).astype(np.int64)
+    tot_s = 0.0
     for _ in range(args.steps):
-        vals.append(cpu_baseline(w, n_sample))
-    tot_cells = n_sample * args.steps
-    tot_s = sum(v["seconds"] for v in vals)
-    value = tot_cells / tot_s
+        tot_s += _oracle_seconds(ora, w, idx, cores)
+    value = per_step * args.steps / tot_s
+    sample = (f"{per_step} cells evenly spaced over the same {n}-cell field per step, one integrate each, "
+              f"{cores} threads (one cell per thread at a time)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["name"], "cells": int(w["T"].shape[0]), "species": 53, "reactions": 325,
-                       "dt_s": w["dt"], "p_atm": 40.0, "rtol": w["rtol"], "atol": w["atol"], "precision": "fp64",
-                       "refine_sweeps": None, "solver": "rosenbrock",
-                       "start": "cold (every step from the initial field)"},
-            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores, "kind": "oracle",
-                             "sample": vals[0]["sample"]},
+            "config": workload_config(w, "fp64", None, "rosenbrock"),
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def algorithmic_flops(steps: np.ndarray, rejects: np.ndarray):
-    """FP64 FLOPs the method needs for the given per-cell step counts (oracle operation count per
-    rate evaluation, Jacobian, LU and solve, with the weights above)."""
+# ------------------------------------------------------------------------------------------------
+# Host-side arithmetic of the line
+
+def _per_part(weights):
     with open(OPCOUNT_FILE) as fh:
         oc = json.load(fh)
-    per = {k: sum(FLOP_WEIGHTS[o] * v[o] for o in FLOP_WEIGHTS) for k, v in oc["counts"].items()}
-    N = oc["N"]
+    return {k: sum(weights[o] * v[o] for o in weights) for k, v in oc["counts"].items()}, oc["N"]
+
+
+def algorithmic_flops(steps: np.ndarray, rejects: np.ndarray, weights=None):
+    """FP64 FLOPs the method needs for the given per-cell step counts (oracle operation count per
+    rate evaluation, Jacobian, LU and solve, with the given operation weights)."""
+    per, N = _per_part(FLOP_WEIGHTS if weights is None else weights)
     # per attempt: W = I/(gamma h) - J (N^2 + N), LU, 4 stage solves + 1 error-filter solve,
     # 2 rate evaluations (stages 2 and 3; stage 4 reuses stage 3), stage combinations and error
     # norm (~ 30 N); per accepted step: one Jacobian (with its own rate evaluation).
@@ -210,6 +267,130 @@ def algorithmic_flops(steps: np.ndarray, rejects: np.ndarray):
     total_attempts = total_steps + int(rejects.sum())
     return attempt * total_attempts + accepted * total_steps, {"per_attempt": attempt, "per_accepted": accepted}
 
+
+def traffic_bytes(n_cells: int):
+    """DRAM bytes of one integrate launch of n_cells from the two-capture fit (None without one)."""
+    if TRAFFIC_FIT is None:
+        return None
+    return TRAFFIC_FIT["fixed"] + TRAFFIC_FIT["per_cell"] * n_cells
+
+
+class Budget:
+    """Wall-time budget of the run: the timed loop takes another step only if it, the steps that
+    would follow, and the work after the loop (`reserve_s`) still fit."""
+
+    def __init__(self, limit_s: float, t0: float = None):
+        self.limit = float(limit_s)
+        self.t0 = T_START if t0 is None else t0
+
+    def elapsed(self, now=None):
+        return (time.monotonic() if now is None else now) - self.t0
+
+    def may_continue(self, done: int, requested: int, step_s: float, reserve_s: float, now=None) -> bool:
+        if done >= requested:
+            return False
+        if done == 0:
+            return True  # at least one timed step
+        return self.elapsed(now) + step_s + reserve_s <= self.limit
+
+
+def workload_config(w, precision, refine_sweeps, solver, **extra):
+    K = w["mech"].K
+    cfg = {"workload": w["name"], "cells": int(w["T"].shape[0]), "species": K, "reactions": w["mech"].R,
+           "dt_s": w["dt"], "p_atm": w["p_Pa"] / 101325.0, "rtol": w["rtol"], "atol": w["atol"],
+           "precision": precision, "refine_sweeps": refine_sweeps, "solver": solver,
+           "start": "cold (every step from the initial field)"}
+    cfg.update(extra)
+    return cfg
+
+
+def roofline_block(steps_np, rej_np, kern_ms_per_launch, peak, rosen, n_cells, traffic_ok):
+    """The `roofline` object of the line: FP64-ALU bound, achieved FLOP/s of one launch from the
+    algorithmic count (unit weights for `frac`, transcendental-weighted beside it)."""
+    if rosen:
+        f_unit, per_unit = algorithmic_flops(steps_np, rej_np, UNIT_WEIGHTS)
+        f_w, per_w = algorithmic_flops(steps_np, rej_np, FLOP_WEIGHTS)
+    else:
+        f_unit = f_w = float("nan")
+        per_unit = per_w = {"per_attempt": None, "per_accepted": None}
+    sec = kern_ms_per_launch / 1e3
+    a_unit = f_unit / sec / 1e12
+    a_w = f_w / sec / 1e12
+    ok = np.isfinite(a_unit)
+    return {"bound": "alu", "achieved": a_unit if ok else None, "peak": peak["tflops"], "unit": "TFLOP/s",
+            "frac": a_unit / peak["tflops"] if ok else None,
+            "traffic": traffic_bytes(n_cells) if traffic_ok else None,
+            "peak_source": peak["source"], "peak_measured": peak["measured_tflops"],
+            "frac_of_measured": a_unit / peak["measured_tflops"] if ok else None,
+            "weights": "add, mul, div, exp, log count 1 flop each",
+            "achieved_weighted": a_w if ok else None,
+            "frac_weighted": a_w / peak["tflops"] if ok else None,
+            "frac_weighted_of_measured": a_w / peak["measured_tflops"] if ok else None,
+            "weights_weighted": "exp 34 and log 62 flops (17 and 31 DFMA of FP64 pipe time)",
+            "flops_per_attempt": per_unit["per_attempt"], "flops_per_accepted_step": per_unit["per_accepted"],
+            "flops_per_attempt_weighted": per_w["per_attempt"],
+            "flops_per_accepted_step_weighted": per_w["per_accepted"]}
+
+
+def forward_line(*, w, world, args, steps_done, kern_ms, e2e, clk, st_np, steps_np, rej_np, peak, opts_info,
+                 dtype, rosen, traffic_ok, lowp_stats, warm_cells, budget_stopped):
+    """The JSON line of the forward workloads from the measured pieces (host arithmetic only)."""
+    n_total = int(w["T"].shape[0])
+    cells = n_total * world * steps_done
+    value = cells / (kern_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": steps_done,
+        "warmup": args.warmup, "ms_per_step": kern_ms / steps_done, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": workload_config(w, args.precision, opts_info.get("refine_sweeps"), args.solver,
+                                  warps_per_cell=opts_info.get("warps_per_cell"),
+                                  cells_per_cta=opts_info.get("cells_per_cta"), cuda_graph=True,
+                                  scheduling="persistent kernel + device work queue",
+                                  l2="flushed between steps (256 MiB write)",
+                                  warmup_cells=warm_cells),
+        "e2e": e2e,
+        "gpu_launches": 1 * steps_done,
+        "roofline": roofline_block(steps_np, rej_np, kern_ms / steps_done, peak, rosen, n_total, traffic_ok),
+        "clocks": clk,
+        "cells_status": {str(k): int(v) for k, v in zip(*np.unique(st_np, return_counts=True))},
+        "steps_per_cell": {"mean": float(steps_np.mean()), "max": int(steps_np.max()),
+                           "rejects_mean": float(rej_np.mean())},
+    }
+    if steps_done != args.steps or budget_stopped:
+        line["steps_requested"] = args.steps
+        line["budget_stop"] = f"timed loop stopped after {steps_done} of {args.steps} steps: wall-time budget " \
+                              f"{args.budget_s:.0f} s"
+    if lowp_stats:
+        line["refinement"] = lowp_stats
+    return line
+
+
+def adjoint_line(*, w, world, args, n, K, R, N, cap, fwd, bwd, tot, clk, ns, st, peak_bytes, warm, h2d, d2h):
+    cells = n * world * args.steps
+    return {
+        "metric": "cells/s, forward with checkpoints + discrete adjoint (53 sp, igniting band, dt 1e-4 s)",
+        "value": cells / ((fwd + bwd) / 1e3), "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": (fwd + bwd) / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "cells": n, "species": K, "reactions": R, "dt_s": w["dt"],
+                   "p_atm": w["p_Pa"] / 101325.0, "rtol": w["rtol"], "atol": w["atol"],
+                   "warmup_cells": warm, "l2": "flushed between steps (256 MiB write)",
+                   "gradient": "dL/d(T0, Y0) per cell and dL/dlnA summed over cells, L random linear"},
+        "forward_ms": fwd / args.steps, "backward_ms": bwd / args.steps, "backward_over_forward": bwd / fwd,
+        "checkpoint": {"bytes_allocated": int(n * cap * (N + 1) * 8), "bytes_used": int(ns.sum()) * (N + 1) * 8,
+                       "steps_per_cell_max": int(ns.max()), "steps_per_cell_mean": float(ns.mean()),
+                       "peak_device_bytes": int(peak_bytes)},
+        "e2e": {"value": cells / (tot / 1e3), "unit": "cells/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": 4 * args.steps,
+        "roofline": None,
+        "clocks": clk,
+        "cells_status": {str(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
+    }
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU workloads
 
 def run_adjoint(args, world, rank, local):
     """Forward with checkpoints + discrete adjoint on the igniting band (see the module doc)."""
@@ -294,31 +475,11 @@ def run_adjoint(args, world, rank, local):
     torch.cuda.synchronize()
     clk = clocks.stop()
     fwd, bwd, tot = ranks.max_over_ranks([fwd, bwd, tot], device="cuda")
-    ns = nsteps.cpu().numpy()
-    st = status.cpu().numpy()
-    cells = n * world * args.steps
-    line = {
-        "metric": "cells/s, forward with checkpoints + discrete adjoint (53 sp, igniting band, dt 1e-4 s)",
-        "value": cells / ((fwd + bwd) / 1e3), "unit": "cells/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": (fwd + bwd) / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w["name"], "cells": n, "species": K, "reactions": R, "dt_s": w["dt"],
-                   "p_atm": w["p_Pa"] / 101325.0, "rtol": w["rtol"], "atol": w["atol"],
-                   "warmup_cells": warm, "l2": "flushed between steps (256 MiB write)",
-                   "gradient": "dL/d(T0, Y0) per cell and dL/dlnA summed over cells, L random linear"},
-        "forward_ms": fwd / args.steps, "backward_ms": bwd / args.steps, "backward_over_forward": bwd / fwd,
-        "checkpoint": {"bytes_allocated": int(n * cap * (N + 1) * 8), "bytes_used": int(ns.sum()) * (N + 1) * 8,
-                       "steps_per_cell_max": int(ns.max()), "steps_per_cell_mean": float(ns.mean()),
-                       "peak_device_bytes": int(torch.cuda.max_memory_allocated())},
-        "e2e": {"value": cells / (tot / 1e3), "unit": "cells/s",
-                "h2d_bytes_per_step": int((T_host.numel() + Y_host.numel() + gT_host.numel() + gY_host.numel()) * 8),
-                "d2h_bytes_per_step": int((n + K * n + R) * 8)},
-        "gpu_launches": 4 * args.steps,
-        "roofline": None,
-        "clocks": clk,
-        **({"refinement": lowp_stats} if lowp_stats else {}),
-        "cells_status": {str(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
-    }
+    line = adjoint_line(w=w, world=world, args=args, n=n, K=K, R=R, N=N, cap=cap, fwd=fwd, bwd=bwd, tot=tot,
+                        clk=clk, ns=nsteps.cpu().numpy(), st=status.cpu().numpy(),
+                        peak_bytes=torch.cuda.max_memory_allocated(), warm=warm,
+                        h2d=(T_host.numel() + Y_host.numel() + gT_host.numel() + gY_host.numel()) * 8,
+                        d2h=(n + K * n + R) * 8)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -403,8 +564,8 @@ def run_ablation(args, world, rank, local):
     return 0
 
 
-def main():
-    args = parse_args()
+def main(argv=None):
+    args = parse_args(argv)
     world, rank, local = dist_setup(args)
     from paper_2105_12070_gb300 import synth
     if args.workload == "adjoint" and args.impl == "gpu":
@@ -417,12 +578,15 @@ def main():
         w = synth.workload_shear_layer()
     if args.dt > 0:
         w["dt"] = args.dt
-    rtol_nominal = w["rtol"]
     if args.rtol > 0:
+        w["rtol_nominal"] = w["rtol"]
         w["rtol"] = args.rtol
     if args.impl == "reference":
         return run_reference(args, w, world, rank)
+    return run_forward(args, w, world, rank, local)
 
+
+def run_forward(args, w, world, rank, local):
     import torch
     from paper_2105_12070_gb300 import chem, ranks
 
@@ -430,12 +594,16 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    rtol_nominal = w.get("rtol_nominal", w["rtol"])
+    budget = Budget(args.budget_s)
     mech = chem.Mechanism(w["mech"].write_temp())
     n_total = w["T"].shape[0] if args.cells <= 0 else args.cells
     # weak scaling: every rank integrates its own copy of the field (cells are independent)
     idx = np.arange(n_total) % w["T"].shape[0]
-    T_host = torch.from_numpy(w["T"][idx].copy()).pin_memory()
-    Y_host = torch.from_numpy(w["Y"][:, idx].copy()).pin_memory()
+    if n_total != w["T"].shape[0]:
+        w = dict(w, T=w["T"][idx].copy(), Y=w["Y"][:, idx].copy(), name=f"{w['name']}_first{n_total}")
+    T_host = torch.from_numpy(w["T"].copy()).pin_memory()
+    Y_host = torch.from_numpy(w["Y"].copy()).pin_memory()
     T_out = torch.empty_like(T_host).pin_memory()
     Y_out = torch.empty_like(Y_host).pin_memory()
     T = torch.empty_like(T_host, device="cuda")
@@ -454,85 +622,104 @@ def main():
         opts.refine_sweeps = args.refine_sweeps
     opts.use_graph = 1
     stream = torch.cuda.current_stream()
-
     lowp_stats = {}
 
-    def one_step(timed: bool, want_stats: bool = False):
+    def device_call(m, want_stats=False, o=None):
+        """T, Y <- the first m cells of the field (outside the events), then one timed call."""
         flush.fill_(1.0)  # L2 flush between steps (outside the events)
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        e[0].record(stream)
-        T.copy_(T_host, non_blocking=True)
-        Y.copy_(Y_host, non_blocking=True)
-        e[1].record(stream)
-        st = chem.chem_integrate(mech, w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], status=status, opts=opts,
+        Ts, Ys = (T, Y) if m == n_total else (T[:m], Y[:, :m])
+        if m == n_total:
+            T.copy_(T_host, non_blocking=True)
+            Y.copy_(Y_host, non_blocking=True)
+        else:
+            Ts = T_host[:m].to("cuda", non_blocking=True)
+            Ys = Y_host[:, :m].contiguous().to("cuda", non_blocking=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = chem.chem_integrate(mech, w["p_Pa"], Ts, Ys, w["dt"], w["rtol"], w["atol"],
+                                 status=status if m == n_total else status[:m], opts=opts if o is None else o,
                                  want_stats=want_stats)
-        e[2].record(stream)
-        if st is not None:
+        e1.record(stream)
+        e1.synchronize()
+        if st is not None and prec != chem.CHEM_PREC_FP64:
             lowp_stats.update(attempts=int(st.steps + st.rejects), refine_fallbacks=int(st.refine_fallbacks))
-        T_out.copy_(T, non_blocking=True)
-        Y_out.copy_(Y, non_blocking=True)
-        e[3].record(stream)
-        e[3].synchronize()
-        return e[1].elapsed_time(e[2]), e[0].elapsed_time(e[3])
+        return e0.elapsed_time(e1)
 
+    warm = min(args.warm_cells, n_total)
     for i in range(args.warmup):
-        # the last warm-up call of a mixed-precision run also reads the refinement fallbacks
-        one_step(False, want_stats=(i == args.warmup - 1 and prec != chem.CHEM_PREC_FP64))
+        device_call(warm, want_stats=(i == args.warmup - 1))
+    # the library's per-cell and staging buffers for the full field, outside the timed region
+    prime = chem.default_opts(max_steps=1)
+    T.copy_(T_host)
+    Y.copy_(Y_host)
+    chem.chem_integrate(mech, w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], status=status, opts=prime)
+    Tp, Yp = T_host[:1].clone().pin_memory(), Y_host[:, :1].clone().pin_memory()
+    if not args.no_e2e:
+        Tp = torch.empty_like(T_host).pin_memory()
+        Yp = torch.empty_like(Y_host).pin_memory()
+        Tp.copy_(T_host)
+        Yp.copy_(Y_host)
+        chem.chem_integrate(mech, w["p_Pa"], Tp, Yp, w["dt"], w["rtol"], w["atol"], opts=prime,
+                            stream=stream.cuda_stream)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    kern_ms, e2e_ms = 0.0, 0.0
-    for _ in range(args.steps):
-        k, e = one_step(True)
-        kern_ms += k
-        e2e_ms += e
+    kern_ms = 0.0
+    done = 0
+    reserve = 60.0 if args.no_cpu_baseline else 120.0  # CPU legs, counters, print
+    stopped = False
+    while True:
+        step_s = kern_ms / 1e3 / done if done else 0.0
+        # the e2e call after the loop costs one more step
+        if not budget.may_continue(done, args.steps, step_s, reserve + (0.0 if args.no_e2e else step_s)):
+            stopped = done < args.steps
+            break
+        kern_ms += device_call(n_total)
+        done += 1
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
-    clk = clocks.stop()
-    kern_ms, e2e_ms = ranks.max_over_ranks([kern_ms, e2e_ms], device="cuda")
+    T_out.copy_(T)
+    Y_out.copy_(Y)
     st_np = status.cpu().numpy()
     steps = torch.zeros(n_total, dtype=torch.int32, device="cuda")
     rej = torch.zeros_like(steps)
     chem.chem_last_cell_counters(mech, steps, rej)
     steps_np, rej_np = steps.cpu().numpy(), rej.cpu().numpy()
-    cells = n_total * world * args.steps
-    value = cells / (kern_ms / 1e3)
-    e2e_value = cells / (e2e_ms / 1e3)
+    # e2e: one call through the C ABI with pinned host arrays; the library stages the field to the
+    # device, integrates and copies the result back inside the call
+    e2e = None
+    if not args.no_e2e:
+        Tp.copy_(T_host)
+        Yp.copy_(Y_host)
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        chem.chem_integrate(mech, w["p_Pa"], Tp, Yp, w["dt"], w["rtol"], w["atol"], opts=opts,
+                            stream=stream.cuda_stream)
+        e2e_s = time.perf_counter() - t0
+        e2e_s = ranks.max_over_ranks([e2e_s], device="cuda")[0]
+        e2e = {"value": n_total * world / e2e_s, "unit": "cells/s",
+               "h2d_bytes_per_step": int(T_host.numel() * 8 + Y_host.numel() * 8),
+               "d2h_bytes_per_step": int(T_host.numel() * 8 + Y_host.numel() * 8),
+               "calls": 1, "how": "host wall time of one chem_integrate call on pinned host arrays (C ABI host path)",
+               "same_result_as_device_path": bool(np.array_equal(Tp.numpy(), T_out.numpy())
+                                                  and np.array_equal(Yp.numpy(), Y_out.numpy()))}
+    clk = clocks.stop()
+    kern_ms = ranks.max_over_ranks([kern_ms], device="cuda")[0]
     rosen = solver == chem.CHEM_SOLVER_ROSENBROCK
-    flops, per = algorithmic_flops(steps_np, rej_np) if (mech.K == 53 and rosen) else (float("nan"), {"per_attempt": None,
-                                                                                      "per_accepted": None})
-    achieved = flops / (kern_ms / 1e3 / args.steps) / 1e12  # TFLOP/s, one launch
     peak = fp64_peak_tflops()
-    line = {
-        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": kern_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {chem.CHEM_PREC_FP64: "f64", chem.CHEM_PREC_MIXED: "f64+f32"}.get(prec, "f64+f32x2"), "data": "synthetic",
-        "config": {"workload": w["name"], "cells": n_total, "species": mech.K, "reactions": mech.R, "dt_s": w["dt"],
-                   "p_atm": w["p_Pa"] / 101325.0, "rtol": w["rtol"], "atol": w["atol"], "precision": args.precision,
-                   "refine_sweeps": opts.refine_sweeps if prec != chem.CHEM_PREC_FP64 else None,
-                   "solver": args.solver,
-                   "warps_per_cell": opts.warps_per_cell, "cells_per_cta": opts.cells_per_cta, "cuda_graph": True,
-                   "scheduling": "persistent kernel + device work queue", "l2": "flushed between steps (256 MiB write)",
-                   "start": "cold (every step from the initial field)"},
-        "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": int(T_host.numel() * 8 + Y_host.numel() * 8),
-                "d2h_bytes_per_step": int(T_out.numel() * 8 + Y_out.numel() * 8)},
-        "gpu_launches": 1 * args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved if np.isfinite(achieved) else None,
-                     "peak": peak["tflops"], "unit": "TFLOP/s",
-                     "frac": achieved / peak["tflops"] if np.isfinite(achieved) else None,
-                     "traffic": (TRAFFIC_BYTES_PER_CELL * n_total
-                                 if (mech.K == 53 and prec == chem.CHEM_PREC_FP64 and rosen) else None),
-                     "peak_source": peak["source"],
-                     "peak_measured": peak["measured_tflops"],
-                     "frac_of_measured": (achieved / peak["measured_tflops"] if np.isfinite(achieved) else None),
-                     "flops_per_attempt": per["per_attempt"], "flops_per_accepted_step": per["per_accepted"]},
-        "clocks": clk,
-        **({"refinement": lowp_stats} if lowp_stats else {}),
-        "cells_status": {str(k): int(v) for k, v in zip(*np.unique(st_np, return_counts=True))},
-        "steps_per_cell": {"mean": float(steps_np.mean()), "max": int(steps_np.max()),
-                           "rejects_mean": float(rej_np.mean())},
-    }
+    line = forward_line(
+        w=w, world=world, args=args, steps_done=done, kern_ms=kern_ms, e2e=e2e, clk=clk, st_np=st_np,
+        steps_np=steps_np, rej_np=rej_np, peak=peak,
+        opts_info={"refine_sweeps": opts.refine_sweeps if prec != chem.CHEM_PREC_FP64 else None,
+                   "warps_per_cell": opts.warps_per_cell, "cells_per_cta": opts.cells_per_cta},
+        dtype={chem.CHEM_PREC_FP64: "f64", chem.CHEM_PREC_MIXED: "f64+f32"}.get(prec, "f64+f32x2"),
+        rosen=rosen and mech.K == 53,
+        traffic_ok=(mech.K == 53 and prec == chem.CHEM_PREC_FP64 and rosen and args.dt <= 0),
+        lowp_stats=lowp_stats, warm_cells=warm, budget_stopped=stopped)
     if args.accuracy_sample > 0:
         # a converged FP64 solution of sampled cells (tight tolerances) on the same GPU path
         m_s = min(args.accuracy_sample, n_total)
@@ -571,7 +758,7 @@ def main():
         Tr, Yr = T_out.numpy(), Y_out.numpy()
         line["reference_mapping"] = {
             "tol_T_K": 1e-6, "tol_Y": 1e-9, "mapped_cells": int(nm), "ms_per_step": mms,
-            "value": n_total / (mms / 1e3), "speedup": (kern_ms / args.steps) / mms,
+            "value": n_total / (mms / 1e3), "speedup": (kern_ms / done) / mms,
             "max_err_vs_solve_in_tol_units": float(max(
                 (np.abs(Tm - Tr) / (w["atol"] + w["rtol"] * np.abs(Tr))).max(),
                 (np.abs(Ym - Yr) / (w["atol"] + w["rtol"] * np.abs(Yr))).max()))}
@@ -593,7 +780,7 @@ def main():
         Tf, Yf = T.cpu().numpy(), Y.cpu().numpy()
         dT = np.abs(T_ref.numpy() - Tf) / np.abs(Tf)
         dY = np.abs(Y_ref.numpy() - Yf)
-        line["vs_fp64"] = {"fp64_ms_per_step": fms, "speedup": fms / (kern_ms / args.steps),
+        line["vs_fp64"] = {"fp64_ms_per_step": fms, "speedup": fms / (kern_ms / done),
                            "max_rel_err_T": float(dT.max()),
                            "max_abs_err_Y": float(dY.max()),
                            "max_err_Y_in_tol_units": float((dY / (w["atol"] + w["rtol"] * np.abs(Yf))).max()),
@@ -625,22 +812,16 @@ def main():
     if args.batch_cells > 0:
         # one launch per batch of consecutive cells, static assignment inside each launch
         bopts = chem.default_opts(precision=prec, use_queue=0, batch_cells=args.batch_cells,
-                                  warps_per_cell=opts.warps_per_cell, cells_per_cta=opts.cells_per_cta)
-        T.copy_(T_host)
-        Y.copy_(Y_host)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        chem.chem_integrate(mech, w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], status=status, opts=bopts)
-        e1.record(stream)
-        e1.synchronize()
-        bms = e0.elapsed_time(e1)
+                                  warps_per_cell=opts.warps_per_cell, cells_per_cta=opts.cells_per_cta,
+                                  solver=solver)
+        bms = device_call(n_total, o=bopts)
         line["batched_launches"] = {"batch_cells": args.batch_cells, "ms_per_step": bms,
-                                    "value": n_total / (bms / 1e3), "queue_speedup": bms / (kern_ms / args.steps)}
+                                    "value": n_total / (bms / 1e3), "queue_speedup": bms / (kern_ms / done)}
     if rank == 0 and not args.no_cpu_baseline:
-        cores = os.cpu_count() or 1
-        line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample or max(4 * cores, 32))
-        line["cpu_baseline"].pop("seconds", None)
+        cb = cpu_baseline(w, args.cpu_seconds)
+        cb.pop("seconds", None)
+        line["cpu_baseline"] = cb
+    line["wall_s"] = budget.elapsed()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -252,6 +252,20 @@ int chem_probe_fp64_peak(double* tflops);
  * 1989) of x[i], n entries, device arrays, asynchronous on `stream`. */
 int chem_debug_exp(const double* x, double* y, int64_t n, void* stream);
 
+/* Diagnostic for the tests: factors n dense N x N matrices (A: n x N x N, row-major, FP64,
+ * 1 <= N <= 128) with the kernels' LU with partial pivoting (the dense LU of Sec. 2.3; ties go to
+ * the lowest row) in the factor precision `precision` (CHEM_PREC_FP64: doubles, CHEM_PREC_MIXED:
+ * floats, CHEM_PREC_MIXED_FF: FP32 pairs), pivot column by pivot column (blocked = 0) or in
+ * panels of 8 columns (blocked = 1), by one cell group of 2 warps per matrix.  Writes per matrix
+ * the factors (N*N entries: the unit lower factor's multipliers below the diagonal, the upper
+ * factor on and above it) to `factors` and the reciprocal pivots (N entries) to `invdiag`, both
+ * in the precision's storage (8 bytes per entry for doubles and pairs, 4 for floats), the row
+ * permutation (N ints: row i of the factors is row perm[i] of the matrix) to `perm`, and 1 if a
+ * pivot was exactly zero, else 0, to `singular` (n ints).  Device arrays, owned by the caller;
+ * asynchronous on `stream`.  Returns CHEM_EINVAL for bad sizes, precision or host pointers. */
+int chem_debug_lu(const double* A, int N, int64_t n, int precision, int blocked, void* factors, void* invdiag,
+                  int32_t* perm, int32_t* singular, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* chem_last_error(void);
 

@@ -1,10 +1,13 @@
 """Builds libchemgpu.so (the C-ABI library of include/chemgpu.h) in-tree for sm_103a.
 
-Three translation units compiled in parallel with nvcc, linked as one shared library:
-  csrc/mech_tables.cpp  -- mechanism reader and table layout (host)
-  csrc/chem_kernels.cu  -- forward kernels, launchers and the extern "C" entry points
-  csrc/adjoint.cu       -- the discrete-adjoint kernels (reverse sweep)
-(csrc/cell_device.cuh holds the device code both kernel files share.)
+Seven translation units compiled in parallel with nvcc, linked as one shared library:
+  csrc/mech_tables.cpp     -- mechanism reader and table layout (host)
+  csrc/chem_kernels.cu     -- rate / Jacobian and mapping kernels, launch shapes, CUDA graphs and
+                              the extern "C" entry points
+  csrc/integrate_g{1,2,4,8}.cu -- the integrate kernels (Rosenbrock, Seulex) for cell groups of
+                              1, 2, 4 and 8 warps (device code in csrc/integrate_device.cuh)
+  csrc/adjoint.cu          -- the discrete-adjoint kernels (reverse sweep)
+(csrc/cell_device.cuh holds the device code the kernel files share.)
 """
 from __future__ import annotations
 
@@ -18,7 +21,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libchemgpu.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["mech_tables.cpp", "chem_kernels.cu", "adjoint.cu"]
+SOURCES = ["mech_tables.cpp", "chem_kernels.cu", "adjoint.cu", "integrate_g1.cu", "integrate_g2.cu", "integrate_g4.cu",
+           "integrate_g8.cu"]
 
 
 def _nvcc():

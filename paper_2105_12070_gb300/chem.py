@@ -85,12 +85,13 @@ def load_library(build_if_missing: bool = True):
                                               ctypes.POINTER(ChemStats), vp]
         lib.chem_integrate_varp.argtypes = [vp, vp, vp, vp, i64, dp, dp, dp, vp, vp, ctypes.POINTER(ChemOpts),
                                             ctypes.POINTER(ChemStats), vp]
+        lib.chem_debug_lu.argtypes = [vp, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp]
         lib.chem_get_lnA.argtypes = [vp, vp]
         lib.chem_set_lnA.argtypes = [vp, vp]
         for name in ("chem_load_mechanism", "chem_mech_dims", "chem_rates", "chem_jacobian", "chem_integrate",
                      "chem_last_cell_counters", "chem_probe_fp64_peak", "chem_integrate_noalloc",
                      "chem_debug_exp", "chem_integrate_record", "chem_adjoint", "chem_get_lnA", "chem_set_lnA",
-                     "chem_integrate_mapped", "chem_integrate_varp"):
+                     "chem_integrate_mapped", "chem_integrate_varp", "chem_debug_lu"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -381,3 +382,35 @@ def chem_debug_exp(x, out, stream=None):
     if rc != 0:
         raise ChemError(lib.chem_last_error().decode())
     return out
+
+
+def chem_debug_lu(A, precision: int = CHEM_PREC_FP64, blocked: bool = False, stream=None):
+    """The kernels' LU with partial pivoting of each matrix of A (n, N, N) float64 (device tensor),
+    in the factor precision of `precision`, column by column or in panels of 8 (blocked), for the
+    tests.  Returns (factors, invdiag, perm, singular): factors (n, N*N) and invdiag (n, N) in the
+    precision's storage (float64; float32; FP32 pairs as (n, N*N, 2) / (n, N, 2) float32), perm
+    (n, N) int32, singular (n,) int32."""
+    import torch
+    lib = load_library()
+    if A.dim() != 3 or A.shape[1] != A.shape[2] or A.dtype != torch.float64 or not A.is_cuda:
+        raise ValueError("A must be a (n, N, N) float64 CUDA tensor")
+    A = A.contiguous()
+    n, N = int(A.shape[0]), int(A.shape[1])
+    dev = A.device
+    if precision == CHEM_PREC_MIXED:
+        F = torch.empty((n, N * N), dtype=torch.float32, device=dev)
+        D = torch.empty((n, N), dtype=torch.float32, device=dev)
+    elif precision == CHEM_PREC_MIXED_FF:
+        F = torch.empty((n, N * N, 2), dtype=torch.float32, device=dev)
+        D = torch.empty((n, N, 2), dtype=torch.float32, device=dev)
+    else:
+        F = torch.empty((n, N * N), dtype=torch.float64, device=dev)
+        D = torch.empty((n, N), dtype=torch.float64, device=dev)
+    P = torch.empty((n, N), dtype=torch.int32, device=dev)
+    S = torch.empty((n,), dtype=torch.int32, device=dev)
+    rc = lib.chem_debug_lu(ctypes.c_void_p(A.data_ptr()), N, n, int(precision), int(bool(blocked)),
+                           ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(P.data_ptr()),
+                           ctypes.c_void_p(S.data_ptr()), _stream(stream, True))
+    if rc != 0:
+        raise ChemError(lib.chem_last_error().decode())
+    return F, D, P, S

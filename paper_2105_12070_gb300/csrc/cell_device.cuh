@@ -914,8 +914,45 @@ __device__ inline double lu_carry(float a) { return (double)a; }
 __device__ inline double lu_carry(FF a) { return __hiloint2double(__float_as_int(a.hi), __float_as_int(a.lo)); }
 template <typename S>
 __device__ inline S lu_recip(double c);
+// 1/a by Newton's iteration for the reciprocal, r <- r + r (1 - m r), on the significand m of a
+// (normalised to +-[1, 2) by replacing the exponent field): the seed is the FP32 approximate
+// reciprocal (rcp.approx) of m's leading 24 bits, relative error below 2^-21; two steps in FP64
+// square the error twice (below 2^-84, under the final rounding), so the result is within one
+// unit in the last place of 1/a.  The exponent is then restored by an integer subtraction.  Four
+// FP64 operations instead of a full division; zero, subnormal, very large, infinite and NaN
+// arguments take the division.
+__device__ inline double rcp_newton(double a) {
+  const long long b = __double_as_longlong(a);
+  const int ef = (int)((b >> 52) & 0x7ff);
+  if (ef < 3 || ef > 2044) return 1.0 / a;
+  const long long mb = (b & (long long)0x800fffffffffffffULL) | (1023LL << 52);
+  const double m = __longlong_as_double(mb);
+  const unsigned hi = (unsigned)((unsigned long long)b >> 32);
+  // m as a float: sign, exponent 127, the top 23 significand bits (truncated)
+  const float mf = __uint_as_float((hi & 0x80000000u) | 0x3f800000u | (unsigned)((b >> 29) & 0x7fffff));
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(mf));
+  // rf in +-[0.5, 1]: the same value as a double, by moving its fields
+  const unsigned fb = __float_as_uint(rf);
+  const long long rb = ((long long)(fb >> 31) << 63) | ((long long)(((fb >> 23) & 0xff) - 127 + 1023) << 52) |
+                       ((long long)(fb & 0x7fffff) << 29);
+  double r = __longlong_as_double(rb);
+  double e = fma(-m, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-m, r, 1.0);
+  r = fma(r, e, r);
+  // 1/a = r 2^-(ef - 1023); r's exponent field is 1022 or 1023, the result's stays in [1, 2043]
+  return __longlong_as_double(__double_as_longlong(r) - ((long long)(ef - 1023) << 52));
+}
+
 template <>
-__device__ inline double lu_recip<double>(double c) { return 1.0 / c; }
+__device__ inline double lu_recip<double>(double c) {
+#ifdef CHEM_LU_RCP_DIVISION
+  return 1.0 / c;
+#else
+  return rcp_newton(c);
+#endif
+}
 template <>
 __device__ inline float lu_recip<float>(double c) { return 1.0f / (float)c; }
 template <>
@@ -1008,6 +1045,132 @@ __device__ bool cell_lu(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* in
   }
   g.sync();
   return ok;
+}
+
+// The same factorisation in panels of 8 columns, with the same pivots and the same operations on
+// every entry in the same order (so the factors are bitwise those of cell_lu):
+//   1. one warp factors the panel (rows k0.., columns k0..k0+7): pivot search by warp shuffles,
+//      the row interchange inside the panel, the reciprocal, the scaled column and the rank-1
+//      updates of the panel's remaining columns, with warp synchronisation only;
+//   2. the group applies the panel's interchanges to every other column and, right of the panel,
+//      forms U12 = L11^-1 A12 (unit lower forward substitution, one column per thread);
+//   3. the group applies the panel's 8 rank-1 updates to the trailing matrix, each entry taking
+//      them in pivot order.
+// Three group barriers per panel instead of four per column.  perm[N] (the spare slot after the
+// permutation; the plan holds K + 2 ints) carries the singular flag from the panel warp.
+template <int G, typename S>
+__device__ bool cell_lu_blocked(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* invdiag) {
+  constexpr int NT = Grp<G>::NT;
+  constexpr int NB = 8;
+  int* singular = perm + N;
+  const int pw = g.lead;
+  for (int k0 = 0; k0 < N; k0 += NB) {
+    const int k1 = min(k0 + NB, N);
+    if (g.warp() == pw) {
+      const int lane = g.lane();
+      if (k0 == 0 && lane == 0) *singular = 0;
+      for (int k = k0; k < k1; ++k) {
+        long long best = -1;
+        int bi = N;
+        for (int i = k + lane; i < N; i += 32) {
+          const long long v = abs_key(A[i * N + k]);
+          if (v > best) { best = v; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const long long ob = __shfl_xor_sync(kFull, best, o);
+          const int oi = __shfl_xor_sync(kFull, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (bi != k && lane < k1 - k0) {
+          const S t = A[k * N + k0 + lane];
+          A[k * N + k0 + lane] = A[bi * N + k0 + lane];
+          A[bi * N + k0 + lane] = t;
+        }
+        __syncwarp();
+        const S inv = lu_recip<S>(lu_carry(A[k * N + k]));
+        if (lane == 0) {
+          piv[k] = bi;
+          invdiag[k] = inv;
+          if (best <= 0) *singular = 1;  // zero column: singular
+        }
+        for (int i = k + 1 + lane; i < N; i += 32) {
+          S* Ai = A + (size_t)i * N;
+          S l = Ai[k];
+          l *= inv;
+          Ai[k] = l;
+          for (int j = k + 1; j < k1; ++j) Ai[j] = fma(-l, A[k * N + j], Ai[j]);
+        }
+        __syncwarp();
+      }
+    }
+    g.sync();
+    for (int j = g.t; j < N; j += NT) {
+      if (j >= k0 && j < k1) continue;
+      for (int k = k0; k < k1; ++k) {
+        const int p = piv[k];
+        if (p != k) {
+          const S t = A[k * N + j];
+          A[k * N + j] = A[p * N + j];
+          A[p * N + j] = t;
+        }
+      }
+      if (j >= k1) {
+        for (int r = k0 + 1; r < k1; ++r) {
+          S acc = A[r * N + j];
+          for (int c = k0; c < r; ++c) acc = fma(-A[r * N + c], A[c * N + j], acc);
+          A[r * N + j] = acc;
+        }
+      }
+    }
+    g.sync();
+    const int mm = N - k1;
+    const int tot = mm * mm;
+    if (tot > 0) {
+      const float inv_m = 1.0f / (float)mm;
+      const S* U = A + (size_t)k0 * N + k1;  // U12, row stride N
+      // two entries per thread and iteration: independent chains of 8 updates
+      int e = g.t;
+      for (; e + NT < tot; e += 2 * NT) {
+        const int i0 = (int)(((float)e + 0.5f) * inv_m), j0 = e - i0 * mm;
+        const int i1 = (int)(((float)(e + NT) + 0.5f) * inv_m), j1 = e + NT - i1 * mm;
+        S* A0 = A + (size_t)(k1 + i0) * N;
+        S* A1 = A + (size_t)(k1 + i1) * N;
+        S a0 = A0[k1 + j0], a1 = A1[k1 + j1];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+          if (k0 + c < k1) {
+            a0 = fma(-A0[k0 + c], U[(size_t)c * N + j0], a0);
+            a1 = fma(-A1[k0 + c], U[(size_t)c * N + j1], a1);
+          }
+        }
+        A0[k1 + j0] = a0;
+        A1[k1 + j1] = a1;
+      }
+      for (; e < tot; e += NT) {
+        const int i0 = (int)(((float)e + 0.5f) * inv_m), j0 = e - i0 * mm;
+        S* A0 = A + (size_t)(k1 + i0) * N;
+        S a0 = A0[k1 + j0];
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+          if (k0 + c < k1) a0 = fma(-A0[k0 + c], U[(size_t)c * N + j0], a0);
+        A0[k1 + j0] = a0;
+      }
+    }
+    g.sync();
+  }
+  // compose the row interchanges: row i of the factors is row perm[i] of the original matrix
+  if (g.t == 32 * pw) {
+    for (int i = 0; i < N; ++i) perm[i] = i;
+    for (int k = 0; k < N; ++k) {
+      const int p = piv[k];
+      const int t = perm[k];
+      perm[k] = perm[p];
+      perm[p] = t;
+    }
+  }
+  g.sync();
+  return *singular == 0;
 }
 
 // x <- A^-1 x with the factors of cell_lu, by one warp with x in registers: lane l holds rows

@@ -1,0 +1,4 @@
+// The integrate kernels (Rosenbrock and Seulex) for cell groups of 2 warps, and their launchers.
+#include "integrate_device.cuh"
+
+CHEM_DEFINE_INTEGRATE_LAUNCHERS(2)
