@@ -9,7 +9,8 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   thermo       -- d(h/R)/dT = cp/R and d(s/R)/dT = cp/(R T) by complex step; continuity at Tmid
   rates        -- closed-form kinetics (A=B, A->B->C), element conservation, enthalpy
                   conservation, Gibbs-minimum equilibrium (independent element-potential solve),
-                  detailed balance at equilibrium, fall-off limits (Pr->0, Pr->inf, F(center))
+                  detailed balance at equilibrium, fall-off limits (Pr->0, Pr->inf, F(center)),
+                  the width of the Troe broadening curve (its half- and fifth-depth points)
   jacobian     -- complex-step derivative of rates to 1e-12 row-normwise, central differences
   integrate    -- Rosenbrock order conditions and L-stability from the coefficient table,
                   closed-form A=B and A->B->C solutions, observed convergence order

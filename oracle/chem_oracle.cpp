@@ -586,9 +586,9 @@ static void troe_F(const Reaction& x, const S& T, const S& Pr, S& F, S& dlog10F_
   S Fcent = S(1.0 - a) * exp(-T / S(T3)) + S(a) * exp(-T / S(T1)) + exp(-S(T2) / T);
   S L = log10_(Fcent);
   S c = S(-0.4) - S(ORACLE_PLANT == 7 ? -0.67 : 0.67) * L;  // plant 7
-  S n = S(0.75) - S(1.27) * L;
+  S n = S(0.75) - S(ORACLE_PLANT == 11 ? -1.27 : 1.27) * L;  // plant 11
   S x10 = log10_(Pr);
-  S den = n - S(0.14) * (x10 + c);
+  S den = n - S(ORACLE_PLANT == 12 ? -0.14 : 0.14) * (x10 + c);  // plant 12
   S f1 = (x10 + c) / den;
   S log10F = L / (S(1.0) + f1 * f1);
   F = pow10_(log10F);

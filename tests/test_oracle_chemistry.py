@@ -199,6 +199,35 @@ def _falloff_mech(troe, params="0.6 200.0 1200.0 5000.0"):
     return path
 
 
+def test_troe_broadening_width():
+    """The width of Troe's broadening curve (Gilbert, Luther & Troe 1983, the CHEMKIN form).  In
+    u = log10 Pr + c the curve is log10 F = log10 Fcent / (1 + f^2), f = u / (n - d u).  Solving
+    f = +1 and f = -1 by hand gives the two half-depth points u = n / (1 + d) and u = -n / (1 - d),
+    where F = Fcent^(1/2) exactly, 2 n / (1 - d^2) apart; f = +-2 gives u = 2n / (1 + 2d) and
+    -2n / (1 - 2d), where F = Fcent^(1/5).  The oracle's rate constants are evaluated at the
+    pressures that put log10 Pr there, over several broadening centres.  The width
+    n = 0.75 - 1.27 log10 Fcent and the slope d = 0.14 set where these points lie, so a wrong sign
+    or term in either moves them off (planted mistakes 11 and 12)."""
+    T = 1300.0
+    Y = np.array([0.3, 0.7])
+    kinf = 1.0e6 * T ** 0.3 * np.exp(-3000.0 / (RC * T))
+    k0 = 1.0e13 * T ** -0.5 * np.exp(-1000.0 / (RC * T))
+    d = 0.14
+    for a, T3, T1, T2 in ((0.6, 200.0, 1200.0, 5000.0), (0.2, 100.0, 3000.0, 9000.0), (0.9, 800.0, 800.0, 2000.0)):
+        ora = O.OracleMechanism(_falloff_mech(True, f"{a} {T3} {T1} {T2}"))
+        Fcent = (1 - a) * np.exp(-T / T3) + a * np.exp(-T / T1) + np.exp(-T2 / T)
+        L = np.log10(Fcent)
+        c = -0.4 - 0.67 * L
+        n = 0.75 - 1.27 * L
+        for u, power in ((n / (1 + d), 0.5), (-n / (1 - d), 0.5), (2 * n / (1 + 2 * d), 0.2),
+                         (-2 * n / (1 - 2 * d), 0.2)):
+            Pr = 10.0 ** (u - c)
+            p = Pr * kinf / k0 * RU * T / 10.0  # [M] = p / (Ru T) with p in dyn/cm^2, efficiencies 1
+            kf = ora.reaction_rates(p, T, Y)[0][0]
+            F = kf / (kinf * Pr / (1 + Pr))
+            assert abs(np.log10(F) / L - power) < 1e-10, (a, u, power, np.log10(F) / L)
+
+
 @pytest.mark.parametrize("troe", [False, True])
 def test_falloff_limits(troe):
     ora = O.OracleMechanism(_falloff_mech(troe))

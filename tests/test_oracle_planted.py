@@ -1,7 +1,7 @@
 """The oracle's pins catch plausible mistakes: each planted mistake fails the pin that guards it.
 
 chem_oracle.cpp compiled with -DORACLE_PLANT=n carries one deliberate error (marked "plant n"
-there).  Three of them are planted consistently in f and in the analytical Jacobian, so the
+there).  Several are planted consistently in f and in the analytical Jacobian, so the
 complex-step Jacobian check cannot see them and a physical pin has to.  A pin fails either at its
 property or earlier, when the integration it runs no longer completes (plants 1, 3 and 5 end
 that way: a cell status other than OK).
@@ -16,6 +16,8 @@ that way: a cell status other than OK).
   8  Rosenbrock weight b_1 off by 1e-3                             -> order conditions
   9  third-body efficiencies ignored in [M]                        -> closed-form A=B with [M]
  10  the Jacobian returned transposed                              -> complex-step Jacobian
+ 11  Troe width n = 0.75 + 1.27 log10 Fcent (rates and J)          -> Troe broadening width
+ 12  Troe slope term n + 0.14 (log10 Pr + c) (rates and J)         -> Troe broadening width
 
 The pins are the functions of test_oracle_chemistry.py and test_oracle_integrator.py, called on
 oracle objects made from the planted build.  The unplanted oracle passes all of them (those
@@ -31,7 +33,7 @@ import test_oracle_chemistry as C
 import test_oracle_integrator as I
 from paper_2105_12070_gb300 import synth
 
-PLANTS = range(1, 11)
+PLANTS = range(1, 13)
 
 
 class _Fixtures:
@@ -86,6 +88,8 @@ GUARD = {
     8: ("Rosenbrock order conditions", lambda s, m: I.test_order_conditions()),
     9: ("closed-form A=B third body", lambda s, m: I.test_closed_form_isomer_third_body()),
     10: ("complex-step Jacobian", lambda s, m: C.test_jacobian_complex_step("mech53", _Fixtures({"mech53": m}))),
+    11: ("Troe broadening width", lambda s, m: C.test_troe_broadening_width()),
+    12: ("Troe broadening width", lambda s, m: C.test_troe_broadening_width()),
 }
 
 
