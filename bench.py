@@ -80,7 +80,7 @@ def parse_args(argv=None):
     ap.add_argument("--cells", type=int, default=0, help="cells per rank (0 = the full field of the workload)")
     ap.add_argument("--warm-cells", type=int, default=608,
                     help="cells of each warm-up call (a slice of the field; 608 = 4 cells on each of 152 SMs)")
-    ap.add_argument("--budget-s", type=float, default=1500.0,
+    ap.add_argument("--budget-s", type=float, default=1650.0,
                     help="wall-time budget of the whole run in seconds (the timed loop stops early if the rest "
                          "cannot finish inside it)")
     ap.add_argument("--dt", type=float, default=0.0, help="override the CFD time step (profiling small cases)")
@@ -91,7 +91,6 @@ def parse_args(argv=None):
                     help="also time one launch per batch of this many cells (static assignment) against the queue")
     ap.add_argument("--autotune", action="store_true", help="pick warps/cell and cells/CTA with the autotuner first")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer call (profiling runs)")
     ap.add_argument("--rtol", type=float, default=0.0, help="override the workload's rtol (work-precision runs)")
     ap.add_argument("--accuracy-sample", type=int, default=0,
                     help="error of the timed result on this many evenly spaced cells against a converged FP64 "
@@ -346,6 +345,7 @@ def forward_line(*, w, world, args, steps_done, kern_ms, e2e, clk, st_np, steps_
                                   warps_per_cell=opts_info.get("warps_per_cell"),
                                   cells_per_cta=opts_info.get("cells_per_cta"), cuda_graph=True,
                                   scheduling="persistent kernel + device work queue",
+                                  call="chem_integrate on pinned host arrays (C ABI host path)",
                                   l2="flushed between steps (256 MiB write)",
                                   warmup_cells=warm_cells),
         "e2e": e2e,
@@ -597,15 +597,18 @@ def run_forward(args, w, world, rank, local):
     rtol_nominal = w.get("rtol_nominal", w["rtol"])
     budget = Budget(args.budget_s)
     mech = chem.Mechanism(w["mech"].write_temp())
-    n_total = w["T"].shape[0] if args.cells <= 0 else args.cells
-    # weak scaling: every rank integrates its own copy of the field (cells are independent)
-    idx = np.arange(n_total) % w["T"].shape[0]
-    if n_total != w["T"].shape[0]:
-        w = dict(w, T=w["T"][idx].copy(), Y=w["Y"][:, idx].copy(), name=f"{w['name']}_first{n_total}")
+    n_field = w["T"].shape[0]
+    n_total = n_field if args.cells <= 0 else args.cells
+    # weak scaling: every rank integrates its own copy of the field (cells are independent); a
+    # smaller --cells takes evenly spaced cells of the field (profiling and parity slices)
+    if n_total < n_field:
+        idx = np.linspace(0, n_field - 1, n_total).astype(np.int64)
+        w = dict(w, T=w["T"][idx].copy(), Y=w["Y"][:, idx].copy(), name=f"{w['name']}_sample{n_total}")
+    elif n_total > n_field:
+        idx = np.arange(n_total) % n_field
+        w = dict(w, T=w["T"][idx].copy(), Y=w["Y"][:, idx].copy(), name=f"{w['name']}_tiled{n_total}")
     T_host = torch.from_numpy(w["T"].copy()).pin_memory()
     Y_host = torch.from_numpy(w["Y"].copy()).pin_memory()
-    T_out = torch.empty_like(T_host).pin_memory()
-    Y_out = torch.empty_like(Y_host).pin_memory()
     T = torch.empty_like(T_host, device="cuda")
     Y = torch.empty_like(Y_host, device="cuda")
     status = torch.zeros(n_total, dtype=torch.int32, device="cuda")
@@ -624,91 +627,74 @@ def run_forward(args, w, world, rank, local):
     stream = torch.cuda.current_stream()
     lowp_stats = {}
 
-    def device_call(m, want_stats=False, o=None):
-        """T, Y <- the first m cells of the field (outside the events), then one timed call."""
-        flush.fill_(1.0)  # L2 flush between steps (outside the events)
-        Ts, Ys = (T, Y) if m == n_total else (T[:m], Y[:, :m])
+    Tp = torch.empty_like(T_host).pin_memory()  # the caller's host arrays of the timed calls
+    Yp = torch.empty_like(Y_host).pin_memory()
+    sp = torch.empty(n_total, dtype=torch.int32).pin_memory()
+
+    def host_call(m, o=None):
+        """One step: the field (its first m cells) copied into pinned host arrays and L2 flushed
+        outside the timing, then one chem_integrate call through the C ABI on those host arrays:
+        the library stages them to the device, integrates and copies the result back.  Returns
+        (device ms of the integrate launch from the library's events on the stream, wall ms of the
+        whole call)."""
         if m == n_total:
-            T.copy_(T_host, non_blocking=True)
-            Y.copy_(Y_host, non_blocking=True)
+            Ta, Ya, sa = Tp, Yp, sp
+            Ta.copy_(T_host)
+            Ya.copy_(Y_host)
         else:
-            Ts = T_host[:m].to("cuda", non_blocking=True)
-            Ys = Y_host[:, :m].contiguous().to("cuda", non_blocking=True)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        st = chem.chem_integrate(mech, w["p_Pa"], Ts, Ys, w["dt"], w["rtol"], w["atol"],
-                                 status=status if m == n_total else status[:m], opts=opts if o is None else o,
-                                 want_stats=want_stats)
-        e1.record(stream)
-        e1.synchronize()
-        if st is not None and prec != chem.CHEM_PREC_FP64:
+            Ta = T_host[:m].clone().pin_memory()
+            Ya = Y_host[:, :m].contiguous().pin_memory()
+            sa = sp[:m]
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = chem.chem_integrate(mech, w["p_Pa"], Ta, Ya, w["dt"], w["rtol"], w["atol"], status=sa,
+                                 opts=opts if o is None else o, want_stats=True, stream=stream.cuda_stream)
+        wall_ms = (time.perf_counter() - t0) * 1e3
+        if prec != chem.CHEM_PREC_FP64:
             lowp_stats.update(attempts=int(st.steps + st.rejects), refine_fallbacks=int(st.refine_fallbacks))
-        return e0.elapsed_time(e1)
+        return st.kernel_ms, wall_ms
 
     warm = min(args.warm_cells, n_total)
     for i in range(args.warmup):
-        device_call(warm, want_stats=(i == args.warmup - 1))
+        host_call(warm)
     # the library's per-cell and staging buffers for the full field, outside the timed region
-    prime = chem.default_opts(max_steps=1)
-    T.copy_(T_host)
-    Y.copy_(Y_host)
-    chem.chem_integrate(mech, w["p_Pa"], T, Y, w["dt"], w["rtol"], w["atol"], status=status, opts=prime)
-    Tp, Yp = T_host[:1].clone().pin_memory(), Y_host[:, :1].clone().pin_memory()
-    if not args.no_e2e:
-        Tp = torch.empty_like(T_host).pin_memory()
-        Yp = torch.empty_like(Y_host).pin_memory()
-        Tp.copy_(T_host)
-        Yp.copy_(Y_host)
-        chem.chem_integrate(mech, w["p_Pa"], Tp, Yp, w["dt"], w["rtol"], w["atol"], opts=prime,
-                            stream=stream.cuda_stream)
+    host_call(n_total, o=chem.default_opts(max_steps=1))
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    kern_ms = 0.0
+    kern_ms, wall_ms = 0.0, 0.0
     done = 0
-    reserve = 60.0 if args.no_cpu_baseline else 120.0  # CPU legs, counters, print
+    reserve = 30.0 if args.no_cpu_baseline else 30.0 + 3.0 * args.cpu_seconds  # CPU legs, counters, print
     stopped = False
     while True:
-        step_s = kern_ms / 1e3 / done if done else 0.0
-        # the e2e call after the loop costs one more step
-        if not budget.may_continue(done, args.steps, step_s, reserve + (0.0 if args.no_e2e else step_s)):
+        step_s = wall_ms / 1e3 / done if done else 0.0
+        if not budget.may_continue(done, args.steps, step_s, reserve):
             stopped = done < args.steps
             break
-        kern_ms += device_call(n_total)
+        k, wms = host_call(n_total)
+        kern_ms += k
+        wall_ms += wms
         done += 1
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    T_out.copy_(T)
-    Y_out.copy_(Y)
-    st_np = status.cpu().numpy()
+    clk = clocks.stop()
+    T_out, Y_out = Tp.clone(), Yp.clone()
+    st_np = sp.numpy().copy()
     steps = torch.zeros(n_total, dtype=torch.int32, device="cuda")
     rej = torch.zeros_like(steps)
     chem.chem_last_cell_counters(mech, steps, rej)
     steps_np, rej_np = steps.cpu().numpy(), rej.cpu().numpy()
-    # e2e: one call through the C ABI with pinned host arrays; the library stages the field to the
-    # device, integrates and copies the result back inside the call
-    e2e = None
-    if not args.no_e2e:
-        Tp.copy_(T_host)
-        Yp.copy_(Y_host)
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        chem.chem_integrate(mech, w["p_Pa"], Tp, Yp, w["dt"], w["rtol"], w["atol"], opts=opts,
-                            stream=stream.cuda_stream)
-        e2e_s = time.perf_counter() - t0
-        e2e_s = ranks.max_over_ranks([e2e_s], device="cuda")[0]
-        e2e = {"value": n_total * world / e2e_s, "unit": "cells/s",
-               "h2d_bytes_per_step": int(T_host.numel() * 8 + Y_host.numel() * 8),
-               "d2h_bytes_per_step": int(T_host.numel() * 8 + Y_host.numel() * 8),
-               "calls": 1, "how": "host wall time of one chem_integrate call on pinned host arrays (C ABI host path)",
-               "same_result_as_device_path": bool(np.array_equal(Tp.numpy(), T_out.numpy())
-                                                  and np.array_equal(Yp.numpy(), Y_out.numpy()))}
-    clk = clocks.stop()
-    kern_ms = ranks.max_over_ranks([kern_ms], device="cuda")[0]
+    kern_ms, wall_ms = ranks.max_over_ranks([kern_ms, wall_ms], device="cuda")
+    e2e = {"value": n_total * world * done / (wall_ms / 1e3), "unit": "cells/s",
+           "h2d_bytes_per_step": int(T_host.numel() * 8 + Y_host.numel() * 8),
+           "d2h_bytes_per_step": int(T_host.numel() * 8 + Y_host.numel() * 8 + n_total * 4),
+           "how": "host wall time of the same timed chem_integrate calls on pinned host arrays (the C ABI's host "
+                  "path: staging copies in and out inside each call); `value` is the device time of their "
+                  "integrate launches"}
     rosen = solver == chem.CHEM_SOLVER_ROSENBROCK
     peak = fp64_peak_tflops()
     line = forward_line(
@@ -814,7 +800,8 @@ def run_forward(args, w, world, rank, local):
         bopts = chem.default_opts(precision=prec, use_queue=0, batch_cells=args.batch_cells,
                                   warps_per_cell=opts.warps_per_cell, cells_per_cta=opts.cells_per_cta,
                                   solver=solver)
-        bms = device_call(n_total, o=bopts)
+        bopts.use_graph = 1
+        bms = host_call(n_total, o=bopts)[0]
         line["batched_launches"] = {"batch_cells": args.batch_cells, "ms_per_step": bms,
                                     "value": n_total / (bms / 1e3), "queue_speedup": bms / (kern_ms / done)}
     if rank == 0 and not args.no_cpu_baseline:

@@ -80,8 +80,9 @@ typedef struct {
   int ctas_per_sm;   /* resident CTAs per SM for the persistent grid; 0 = automatic */
   int warps_per_cell; /* 1, 2, 4 or 8 warps cooperate on one cell; 0 = automatic */
   int use_graph;      /* 1: launch through a CUDA graph that the library captures once for this
-                         exact argument set and replays on identical calls (device arrays only);
-                         0 (default): direct launches */
+                         exact argument set and replays on identical calls (host arrays: the
+                         graph holds the launches on the library's staging buffers, the copies
+                         stay outside it); 0 (default): direct launches */
   int batch_cells;    /* > 0: split the cells into consecutive batches of this many cells, one
                          kernel launch per batch (the one-launch-per-batch comparison of the
                          persistent queue); 0 (default): one launch for all cells */
@@ -94,6 +95,10 @@ typedef struct {
   int64_t rejects;      /* rejected step attempts */
   int64_t failed_cells; /* cells whose status is not CHEM_CELL_OK */
   int64_t refine_fallbacks; /* mixed precision: stage solves that fell back to an FP64 factor */
+  double kernel_ms;     /* device time of the call's integrate launches in milliseconds: CUDA events
+                           on `stream` around them, after any host-to-device staging and before the
+                           copy back (chem_integrate and the entry points built on it; 0 from
+                           chem_integrate_noalloc, which records no events) */
 } chem_stats;
 
 /* Fill `opts` with the defaults. */
@@ -126,6 +131,11 @@ int chem_describe_mechanism(const char* path, char* buf, int64_t cap, int64_t* n
 
 /* Number of species K (= state length N) and reactions R. */
 int chem_mech_dims(const chem_mech* mech, int* K, int* R);
+
+/* Reaction-type counts of a loaded mechanism: plain third-body reactions and fall-off
+ * (Lindemann or Troe) reactions; their sum is the number of pressure-dependent reactions, which
+ * sets the size of the per-cell working set with K and R.  Either pointer may be NULL. */
+int chem_mech_counts(const chem_mech* mech, int* n_third_body, int* n_falloff);
 
 /* Source term f of Eq. 1 for ncells cells at pressure p_Pa:
  *   dPhidt[0 * ncells + c] = dT/dt, dPhidt[(1 + k) * ncells + c] = dY_k/dt for k < K-1.
@@ -165,7 +175,11 @@ int chem_integrate(const chem_mech* mech, double p_Pa, double* T, double* Y, int
  *   - the library looks the array's device address up the first time the entry point runs on a
  *     device (cudaGetSymbolAddress), so make that first call before any stream capture;
  *   - all calls share that array: it is reset at the start of each call, and two calls whose
- *     work overlaps on the GPU (different streams, no ordering between them) race on it.
+ *     work overlaps on the GPU (different streams, no ordering between them) race on it;
+ *   - opts->batch_cells and opts->use_graph are ignored: the call is always one launch over all
+ *     cells, enqueued directly on `stream` (no library-owned CUDA graph, which would allocate);
+ *   - the per-cell counters go to steps / rejects only: chem_last_cell_counters keeps reporting
+ *     the last chem_integrate on the handle.
  * It allocates nothing itself; the mechanism handle, loaded beforehand, owns its tables. */
 int chem_integrate_noalloc(const chem_mech* mech, double p_Pa, double* T, double* Y, int64_t ncells, double dt,
                            double rtol, double atol, double* h_inout, int32_t* status, int32_t* steps,
@@ -255,15 +269,18 @@ int chem_debug_exp(const double* x, double* y, int64_t n, void* stream);
 /* Diagnostic for the tests: factors n dense N x N matrices (A: n x N x N, row-major, FP64,
  * 1 <= N <= 128) with the kernels' LU with partial pivoting (the dense LU of Sec. 2.3; ties go to
  * the lowest row) in the factor precision `precision` (CHEM_PREC_FP64: doubles, CHEM_PREC_MIXED:
- * floats, CHEM_PREC_MIXED_FF: FP32 pairs), pivot column by pivot column (blocked = 0) or in
- * panels of 8 columns (blocked = 1), by one cell group of 2 warps per matrix.  Writes per matrix
+ * floats, CHEM_PREC_MIXED_FF: FP32 pairs) in one of its three schedules, by one cell group of 2
+ * warps per matrix: variant 0 column by column with four group barriers per column, 1 with two
+ * (the pivot search of the next column fused into the trailing update; the integrate kernels'
+ * default), 2 in panels of 8 columns.  All three give bitwise the same results.  Writes per matrix
  * the factors (N*N entries: the unit lower factor's multipliers below the diagonal, the upper
  * factor on and above it) to `factors` and the reciprocal pivots (N entries) to `invdiag`, both
  * in the precision's storage (8 bytes per entry for doubles and pairs, 4 for floats), the row
  * permutation (N ints: row i of the factors is row perm[i] of the matrix) to `perm`, and 1 if a
  * pivot was exactly zero, else 0, to `singular` (n ints).  Device arrays, owned by the caller;
- * asynchronous on `stream`.  Returns CHEM_EINVAL for bad sizes, precision or host pointers. */
-int chem_debug_lu(const double* A, int N, int64_t n, int precision, int blocked, void* factors, void* invdiag,
+ * asynchronous on `stream`.  Returns CHEM_EINVAL for bad sizes, precision, variant or host
+ * pointers. */
+int chem_debug_lu(const double* A, int N, int64_t n, int precision, int variant, void* factors, void* invdiag,
                   int32_t* perm, int32_t* singular, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -38,7 +38,7 @@ class ChemOpts(ctypes.Structure):
 
 class ChemStats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("rejects", ctypes.c_int64), ("failed_cells", ctypes.c_int64),
-                ("refine_fallbacks", ctypes.c_int64)]
+                ("refine_fallbacks", ctypes.c_int64), ("kernel_ms", ctypes.c_double)]
 
 
 class ChemError(RuntimeError):
@@ -68,6 +68,7 @@ def load_library(build_if_missing: bool = True):
         lib.chem_free_mechanism.argtypes = [vp]
         lib.chem_describe_mechanism.argtypes = [ctypes.c_char_p, ctypes.c_char_p, i64, ctypes.POINTER(i64)]
         lib.chem_mech_dims.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip)]
+        lib.chem_mech_counts.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip)]
         lib.chem_rates.argtypes = [vp, dp, vp, vp, i64, vp, vp]
         lib.chem_jacobian.argtypes = [vp, dp, vp, vp, i64, vp, vp]
         lib.chem_integrate.argtypes = [vp, dp, vp, vp, i64, dp, dp, dp, vp, vp, ctypes.POINTER(ChemOpts),
@@ -88,7 +89,7 @@ def load_library(build_if_missing: bool = True):
         lib.chem_debug_lu.argtypes = [vp, ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp]
         lib.chem_get_lnA.argtypes = [vp, vp]
         lib.chem_set_lnA.argtypes = [vp, vp]
-        for name in ("chem_load_mechanism", "chem_mech_dims", "chem_rates", "chem_jacobian", "chem_integrate",
+        for name in ("chem_load_mechanism", "chem_mech_dims", "chem_mech_counts", "chem_rates", "chem_jacobian", "chem_integrate",
                      "chem_last_cell_counters", "chem_probe_fp64_peak", "chem_integrate_noalloc",
                      "chem_debug_exp", "chem_integrate_record", "chem_adjoint", "chem_get_lnA", "chem_set_lnA",
                      "chem_integrate_mapped", "chem_integrate_varp", "chem_debug_lu"):
@@ -152,6 +153,10 @@ class Mechanism:
         K, R = ctypes.c_int(), ctypes.c_int()
         _check(self._lib.chem_mech_dims(self._h, ctypes.byref(K), ctypes.byref(R)))
         self.K, self.R, self.N = K.value, R.value, K.value
+        ntb, nfo = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.chem_mech_counts(self._h, ctypes.byref(ntb), ctypes.byref(nfo)))
+        self.n_third_body, self.n_falloff = ntb.value, nfo.value
+        self.n_pd = ntb.value + nfo.value
         self.path = path
 
     @property
@@ -384,10 +389,10 @@ def chem_debug_exp(x, out, stream=None):
     return out
 
 
-def chem_debug_lu(A, precision: int = CHEM_PREC_FP64, blocked: bool = False, stream=None):
+def chem_debug_lu(A, precision: int = CHEM_PREC_FP64, variant: int = 0, stream=None):
     """The kernels' LU with partial pivoting of each matrix of A (n, N, N) float64 (device tensor),
-    in the factor precision of `precision`, column by column or in panels of 8 (blocked), for the
-    tests.  Returns (factors, invdiag, perm, singular): factors (n, N*N) and invdiag (n, N) in the
+    in the factor precision of `precision`, in schedule `variant` (0 column by column, 1 with the
+    next pivot search fused into the update, 2 in panels of 8 columns), for the tests.  Returns (factors, invdiag, perm, singular): factors (n, N*N) and invdiag (n, N) in the
     precision's storage (float64; float32; FP32 pairs as (n, N*N, 2) / (n, N, 2) float32), perm
     (n, N) int32, singular (n,) int32."""
     import torch
@@ -408,7 +413,7 @@ def chem_debug_lu(A, precision: int = CHEM_PREC_FP64, blocked: bool = False, str
         D = torch.empty((n, N), dtype=torch.float64, device=dev)
     P = torch.empty((n, N), dtype=torch.int32, device=dev)
     S = torch.empty((n,), dtype=torch.int32, device=dev)
-    rc = lib.chem_debug_lu(ctypes.c_void_p(A.data_ptr()), N, n, int(precision), int(bool(blocked)),
+    rc = lib.chem_debug_lu(ctypes.c_void_p(A.data_ptr()), N, n, int(precision), int(variant),
                            ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(P.data_ptr()),
                            ctypes.c_void_p(S.data_ptr()), _stream(stream, True))
     if rc != 0:

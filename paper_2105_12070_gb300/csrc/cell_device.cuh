@@ -253,7 +253,7 @@ struct Grp {
 struct Plan {
   int N, K, R, n_pd, G;
   int SA;  // size of each of the two matrix buffers: max(N*N, 8*R)
-  int off_A, off_B, off_vec, off_sp, off_q, off_M, off_piv, off_red, total;
+  int off_A, off_B, off_vec, off_sp, off_q, off_M, off_piv, off_red, off_bc, total;
 };
 
 __host__ __device__ inline int round2(int x) { return (x + 1) & ~1; }
@@ -273,8 +273,8 @@ __host__ __device__ inline Plan make_plan(int K, int R, int n_pd, int G) {
   p.off_M = p.off_q + round2(R);
   p.off_piv = p.off_M + round2(max(n_pd, 1));
   p.off_red = p.off_piv + round2(K + 2);  // pivots and the composed permutation (ints)
-  p.total = p.off_red + 6 * G + 2;  // reduction scratch + queue slot
-  p.total = round2(p.total);
+  p.off_bc = p.off_red + 6 * G + 2;  // reduction scratch + queue slot
+  p.total = round2(p.off_bc + 10);     // broadcast slot of the cell scalars (5 values, dual-sized)
   return p;
 }
 
@@ -284,7 +284,7 @@ struct CellMem {
   int *er, *ec;
   float* invd32;
   double *C, *hRT, *cpR, *gRT, *omega, *dcpR;
-  double *q, *M, *red;
+  double *q, *M, *red, *bc;
   int* piv;
   int* perm;
   int* slot;
@@ -312,6 +312,7 @@ __device__ inline CellMem carve(double* base, const Plan& p) {
   w.perm = w.piv + p.K + 2;
   w.red = base + p.off_red;
   w.slot = reinterpret_cast<int*>(base + p.off_red + 6 * p.G);
+  w.bc = base + p.off_bc;
   return w;
 }
 
@@ -323,6 +324,7 @@ struct EvalMem {
   S *q, *M;                               // net rates [R]; [M] of the pressure-dependent [n_pd]
   S *zc, *dwT, *rowA, *rowB, *ccol, *wq;  // Jacobian temporaries [K]
   S* pv;                                  // efficiency-pair coefficients [n_pairs]
+  S* bc = nullptr;                        // broadcast slot of the cell scalars [5] (or none)
 };
 
 // The solve's evaluation arrays: the Jacobian temporaries reuse the stage vectors, which are
@@ -333,6 +335,7 @@ __device__ inline EvalMem<double> eval_mem(const CellMem& w) {
   e.q = w.q; e.M = w.M;
   e.zc = w.zc; e.dwT = w.dwT; e.rowA = w.rowA; e.rowB = w.rowB; e.ccol = w.ccol; e.wq = w.res;
   e.pv = w.u[0];
+  e.bc = w.bc;
   return e;
 }
 
@@ -465,8 +468,6 @@ __device__ CellScalarsT<S> cell_rates(const DevMech& m, const Grp<G>& g, double 
   const int K = m.K, d = K - 1;
   CellScalarsT<S> s;
   s.T = y[0];
-  s.invT = 1.0 / s.T;
-  s.lnT = log(s.T);
   // mass fractions, mean molar mass, density, concentrations, thermo
   S ysum = cst<S>(0.0), yw = cst<S>(0.0);
   for (int k = g.t; k < d; k += NT) {
@@ -477,9 +478,31 @@ __device__ CellScalarsT<S> cell_rates(const DevMech& m, const Grp<G>& g, double 
   g.sum2(ysum, yw);
   const S Yd = 1.0 - ysum;
   yw += Yd * m.sp[d * kSpDoubles + 1];
-  s.Wbar = 1.0 / yw;
-  s.rho = p * s.Wbar / (kRu * s.T);
-  s.inv_rho = yw * kRu * s.T / p;
+  // the cell scalars: ln T and three quotients.  An FP64 instruction costs a warp the same for one
+  // lane as for 32, so with a broadcast slot one thread computes them for the whole group and the
+  // other warps read them back instead of paying for them again (the same operations either way).
+  if (G > 1 && w.bc) {
+    if (g.t == 0) {
+      w.bc[0] = 1.0 / s.T;
+      w.bc[1] = log(s.T);
+      const S Wbar = 1.0 / yw;
+      w.bc[2] = Wbar;
+      w.bc[3] = p * Wbar / (kRu * s.T);
+      w.bc[4] = yw * kRu * s.T / p;
+    }
+    g.sync();
+    s.invT = w.bc[0];
+    s.lnT = w.bc[1];
+    s.Wbar = w.bc[2];
+    s.rho = w.bc[3];
+    s.inv_rho = w.bc[4];
+  } else {
+    s.invT = 1.0 / s.T;
+    s.lnT = log(s.T);
+    s.Wbar = 1.0 / yw;
+    s.rho = p * s.Wbar / (kRu * s.T);
+    s.inv_rho = yw * kRu * s.T / p;
+  }
   S cp = cst<S>(0.0), dcp = cst<S>(0.0);
   for (int k = g.t; k < K; k += NT) {
     const double* sp = m.sp + k * kSpDoubles;
@@ -850,16 +873,43 @@ __device__ void cell_jacobian_vjp(const DevMech& m, const Grp<G>& g, const CellS
 // which GB300 issues at 64 times the FP64 rate.  The FP32 operations are the IEEE-rounded
 // intrinsics, so the compiler cannot contract them and the error-free transformations stay
 // exact.  Used for the factors and the substitutions of CHEM_PREC_MIXED_FF.
+// Conversions between FP64 and FP32 in integer arithmetic (the FP64 pipe, which bounds the
+// kernels, is not used for them).  f32_of rounds to nearest, ties to even, on the 29 bits below
+// the float significand (a carry runs into the exponent); magnitudes below the smallest normal
+// float give a signed zero and above the largest finite float infinity.  f64_of is exact for
+// normal floats, zeros, infinities and NaNs; subnormal floats give a signed zero.
+__device__ inline float f32_of(double v) {
+  const long long b = __double_as_longlong(v);
+  const unsigned sign = (unsigned)((unsigned long long)b >> 63) << 31;
+  const long long mag = b & 0x7fffffffffffffffLL;
+  if (mag >= 0x7ff0000000000000LL) return __uint_as_float(sign | 0x7f800000u | (mag > 0x7ff0000000000000LL));
+  const long long r = mag + 0x0fffffffLL + ((mag >> 29) & 1);
+  const long long fb = (r >> 29) - ((long long)(1023 - 127) << 23);
+  if (fb < (1LL << 23)) return __uint_as_float(sign);
+  if (fb >= 0x7f800000LL) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | (unsigned)fb);
+}
+__device__ inline double f64_of(float f) {
+  const unsigned fb = __float_as_uint(f);
+  const unsigned e = (fb >> 23) & 0xff;
+  const unsigned long long sign = (unsigned long long)(fb >> 31) << 63;
+  const unsigned long long ed = (e == 0) ? 0ULL : (e == 0xff) ? 0x7ffULL : (unsigned long long)(e + 896);
+  const unsigned long long mant = (e == 0) ? 0ULL : (unsigned long long)(fb & 0x7fffff) << 29;
+  return __longlong_as_double((long long)(sign | (ed << 52) | mant));
+}
+
 struct FF {
   float hi, lo;
   FF() = default;
   __device__ FF(float h, float l) : hi(h), lo(l) {}
-  // nearest pair to an FP64 value (hi = fl32(x), lo = fl32(x - hi); x - hi is exact in FP64)
+  // nearest pair to an FP64 value (hi = fl32(x), lo = fl32(x - hi); x - hi is exact in FP64).
+  // This one keeps the conversion instructions: through f32_of / f64_of it put a ~300-byte stack
+  // frame (local memory) on the integrate kernel.
   __device__ explicit FF(double x) {
     hi = __double2float_rn(x);
     lo = __double2float_rn(x - (double)hi);
   }
-  __device__ explicit operator double() const { return (double)hi + (double)lo; }
+  __device__ explicit operator double() const { return f64_of(hi) + f64_of(lo); }
 };
 
 // s + e = a + b exactly (Knuth's two-sum; no ordering of |a|, |b| needed)
@@ -910,7 +960,7 @@ __device__ inline FF shfl(FF v, int l) { return FF(__shfl_sync(kFull, v.hi, l), 
 // FP32 factors (exact), the bit pattern of the pair for FP32 pairs; lu_recip turns it into
 // the reciprocal in the factor type.
 __device__ inline double lu_carry(double a) { return a; }
-__device__ inline double lu_carry(float a) { return (double)a; }
+__device__ inline double lu_carry(float a) { return f64_of(a); }
 __device__ inline double lu_carry(FF a) { return __hiloint2double(__float_as_int(a.hi), __float_as_int(a.lo)); }
 template <typename S>
 __device__ inline S lu_recip(double c);
@@ -954,7 +1004,7 @@ __device__ inline double lu_recip<double>(double c) {
 #endif
 }
 template <>
-__device__ inline float lu_recip<float>(double c) { return 1.0f / (float)c; }
+__device__ inline float lu_recip<float>(double c) { return 1.0f / f32_of(c); }
 template <>
 __device__ inline FF lu_recip<FF>(double c) {
   return ff_recip(FF(__int_as_float(__double2hiint(c)), __int_as_float(__double2loint(c))));
@@ -965,7 +1015,8 @@ __device__ inline FF lu_recip<FF>(double c) {
 // exactly zero pivot.
 
 // |a| as an ordered integer key (bit pattern of a non-negative float / double)
-__device__ inline long long abs_key(double a) { return __double_as_longlong(fabs(a)); }
+// (the sign bit masked off in the integer pipe, so that no FP64 instruction is spent on it)
+__device__ inline long long abs_key(double a) { return __double_as_longlong(a) & 0x7fffffffffffffffLL; }
 __device__ inline long long abs_key(float a) { return (long long)__float_as_int(fabsf(a)); }
 __device__ inline long long abs_key(FF a) { return (long long)__float_as_int(fabsf(a.hi)); }
 
@@ -1029,6 +1080,161 @@ __device__ bool cell_lu(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* in
         const int i = (int)(((float)e + 0.5f) * inv_m);
         const int j = e - i * mm;
         T0[i * N + j] = fma(-Ak[i * N], U[j], T0[i * N + j]);
+      }
+    }
+    g.sync();
+  }
+  // compose the row interchanges: row i of the factors is row perm[i] of the original matrix
+  if (g.t == 32 * g.aux) {
+    for (int i = 0; i < N; ++i) perm[i] = i;
+    for (int k = 0; k < N; ++k) {
+      const int p = piv[k];
+      const int t = perm[k];
+      perm[k] = perm[p];
+      perm[p] = t;
+    }
+  }
+  g.sync();
+  return ok;
+}
+
+// The same factorisation with two group barriers per pivot column instead of four (the same
+// pivots and the same operations on every entry in the same order, so the factors are bitwise
+// those of cell_lu):
+//   * the pivot search of column k+1 rides on step k's trailing update: each thread that updates
+//     an entry of column k+1 keeps the largest |a| it produced, the warps reduce by shuffles and
+//     leave one (key, row) each in the reduction scratch, and the barrier that ends the update
+//     also publishes them;
+//   * every thread then combines the G candidates itself (ties to the lowest row) and takes the
+//     pivot's reciprocal, so no thread waits for another to compute it;
+//   * the row interchange (threads over columns) and the scaled multipliers of column k (threads
+//     over rows, reading the interchanged value for the pivot row) form one phase.
+template <int G, typename S>
+__device__ bool cell_lu_fused(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* invdiag) {
+  constexpr int NT = Grp<G>::NT;
+  double* cand = g.red;  // [2 halves][G][3]: key bits, row and carried value of each warp's best entry
+  bool ok = true;
+  // pivot candidates of column 0
+  {
+    long long best = -1;
+    int bi = N;
+    double bv = 0.0;
+    for (int i = g.t; i < N; i += NT) {
+      const S a = A[i * N];
+      const long long v = abs_key(a);
+      if (v > best) { best = v; bi = i; bv = lu_carry(a); }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long ob = __shfl_xor_sync(kFull, best, o);
+      const int oi = __shfl_xor_sync(kFull, bi, o);
+      const double ov = __shfl_xor_sync(kFull, bv, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; bv = ov; }
+    }
+    if (g.lane() == 0) {
+      cand[3 * g.warp()] = __longlong_as_double(best);
+      cand[3 * g.warp() + 1] = __int2double_rn(bi);
+      cand[3 * g.warp() + 2] = bv;
+    }
+  }
+  g.sync();
+  for (int k = 0; k < N; ++k) {
+    const double* cr = cand + (k & 1) * 3 * G;
+    long long best = __double_as_longlong(cr[0]);
+    int bi = (int)cr[1];
+    double bv = cr[2];
+#pragma unroll
+    for (int w = 1; w < G; ++w) {
+      const long long ob = __double_as_longlong(cr[3 * w]);
+      const int oi = (int)cr[3 * w + 1];
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; bv = cr[3 * w + 2]; }
+    }
+    if (best <= 0) ok = false;  // zero column: singular
+    // interchange rows k and bi in every other column; scaled multipliers of column k (the pivot
+    // row's multiplier is the old row k's entry, and the pivot moves to the diagonal)
+    if (bi != k)
+      for (int j = g.t; j < N; j += NT) {
+        if (j == k) continue;
+        const S t = A[k * N + j];
+        A[k * N + j] = A[bi * N + j];
+        A[bi * N + j] = t;
+      }
+    if (k + 1 + 32 * g.warp() < N || g.t == 0) {  // this warp scales a row, or records the pivot
+      const S inv = lu_recip<S>(bv);
+      if (g.t == 0) {
+        piv[k] = bi;
+        invdiag[k] = inv;
+      }
+      for (int i = k + 1 + g.t; i < N; i += NT) {
+        S v;
+        if (i == bi) {
+          v = A[k * N + k];
+          A[k * N + k] = A[bi * N + k];
+        } else {
+          v = A[i * N + k];
+        }
+        v *= inv;
+        A[i * N + k] = v;
+      }
+    }
+    g.sync();
+    // trailing update: column k+1 first (its entries are the next pivot's candidates, each thread
+    // keeping the largest it produced), then the other columns
+    const int mm = N - k - 1;
+    long long nb = -1;
+    int ni = N;
+    double nv = 0.0;
+    if (mm > 0) {
+      const S* Ak = A + (size_t)(k + 1) * N + k;  // multipliers of the trailing rows
+      const S* U = A + (size_t)k * N + k + 1;     // pivot row right of the diagonal
+      S* T0 = A + (size_t)(k + 1) * N + k + 1;
+      const S u0 = U[0];
+      for (int i = g.t; i < mm; i += NT) {
+        const S r = fma(-Ak[i * N], u0, T0[i * N]);
+        T0[i * N] = r;
+        const long long v = abs_key(r);
+        if (v > nb) { nb = v; ni = k + 1 + i; nv = lu_carry(r); }
+      }
+      const int mc = mm - 1;  // columns k+2 .. N-1
+      const int tot = mm * mc;
+      if (tot > 0) {
+        const float inv_m = 1.0f / (float)mc;
+        int e = g.t;
+        for (; e + 3 * NT < tot; e += 4 * NT) {
+          int ii[4], jj[4];
+          S l[4], u[4], a[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int x = e + q * NT;
+            ii[q] = (int)(((float)x + 0.5f) * inv_m);
+            jj[q] = x - ii[q] * mc + 1;
+            l[q] = Ak[ii[q] * N];
+            u[q] = U[jj[q]];
+            a[q] = T0[ii[q] * N + jj[q]];
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) T0[ii[q] * N + jj[q]] = fma(-l[q], u[q], a[q]);
+        }
+        for (; e < tot; e += NT) {
+          const int i = (int)(((float)e + 0.5f) * inv_m);
+          const int j = e - i * mc + 1;
+          T0[i * N + j] = fma(-Ak[i * N], U[j], T0[i * N + j]);
+        }
+      }
+    }
+    if (k + 1 < N) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long ob = __shfl_xor_sync(kFull, nb, o);
+        const int oi = __shfl_xor_sync(kFull, ni, o);
+        const double ov = __shfl_xor_sync(kFull, nv, o);
+        if (ob > nb || (ob == nb && oi < ni)) { nb = ob; ni = oi; nv = ov; }
+      }
+      if (g.lane() == 0) {
+        double* cw = cand + ((k + 1) & 1) * 3 * G;
+        cw[3 * g.warp()] = __longlong_as_double(nb);
+        cw[3 * g.warp() + 1] = __int2double_rn(ni);
+        cw[3 * g.warp() + 2] = nv;
       }
     }
     g.sync();
@@ -1173,6 +1379,37 @@ __device__ bool cell_lu_blocked(const Grp<G>& g, S* A, int N, int* piv, int* per
   return *singular == 0;
 }
 
+// The factorisation the integrate kernels use: 0 = cell_lu (column by column), 1 = cell_lu_fused,
+// 2 = cell_lu_blocked; all three give bitwise the same factors.  The default is the measured
+// fastest per factor type (fused for FP64 and FP32 pairs, blocked for FP32, whose short FP32
+// chains leave the barriers as the cost); CHEM_LU_VARIANT forces one for every type.
+template <typename S>
+__host__ __device__ constexpr int lu_variant_for() {
+#ifdef CHEM_LU_VARIANT
+  return CHEM_LU_VARIANT;
+#else
+  return std::is_same<S, float>::value ? 2 : 1;
+#endif
+}
+template <int V, int G, typename S>
+__device__ inline bool cell_lu_v(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* invdiag) {
+  if constexpr (V == 1) return cell_lu_fused<G, S>(g, A, N, piv, perm, invdiag);
+  else if constexpr (V == 2) return cell_lu_blocked<G, S>(g, A, N, piv, perm, invdiag);
+  else return cell_lu<G, S>(g, A, N, piv, perm, invdiag);
+}
+// the kernels' schedule for factor type S
+template <int G, typename S>
+__device__ inline bool cell_lu_default(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* invdiag) {
+  return cell_lu_v<lu_variant_for<S>(), G, S>(g, A, N, piv, perm, invdiag);
+}
+// any schedule, chosen at run time (the LU probe of the tests)
+template <int G, typename S>
+__device__ inline bool cell_lu_any(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* invdiag, int variant) {
+  if (variant == 1) return cell_lu_fused<G, S>(g, A, N, piv, perm, invdiag);
+  if (variant == 2) return cell_lu_blocked<G, S>(g, A, N, piv, perm, invdiag);
+  return cell_lu<G, S>(g, A, N, piv, perm, invdiag);
+}
+
 // x <- A^-1 x with the factors of cell_lu, by one warp with x in registers: lane l holds rows
 // l, l+32, .. (S slots, N <= 32 S), so a column step is a shuffle and one FMA per slot that
 // still holds rows below (forward) or above (backward) the column, without shared-memory round
@@ -1180,6 +1417,19 @@ __device__ bool cell_lu_blocked(const Grp<G>& g, S* A, int N, int* piv, int* per
 // issued for a slot with no active row.  perm is the composed row permutation of the LU.
 // T is double (FP64 factors), float or FF (mixed precision; then b is scaled by 2^-er on entry
 // and the result by 2^-ec on exit, the equilibration of form_and_factor_low).
+// FP64 <-> the factor type of the substitutions, without FP64 conversion instructions
+template <typename T>
+__device__ inline T low_of(double v);
+template <>
+__device__ inline double low_of<double>(double v) { return v; }
+template <>
+__device__ inline float low_of<float>(double v) { return f32_of(v); }
+template <>
+__device__ inline FF low_of<FF>(double v) { return FF(v); }
+__device__ inline double high_of(double v) { return v; }
+__device__ inline double high_of(float v) { return f64_of(v); }
+__device__ inline double high_of(FF v) { return (double)v; }
+
 template <int S, typename T>
 __device__ void warp_lu_solve_s(const T* A, int N, const int* perm, const T* invdiag, const int* er, const int* ec,
                                 const double* b, double* x) {
@@ -1191,7 +1441,7 @@ __device__ void warp_lu_solve_s(const T* A, int N, const int* perm, const T* inv
     T v = T(0);
     if (i < N) {
       const int pi = perm[i];
-      v = er ? (T)(b[pi] * pow2(-er[pi])) : (T)b[pi];
+      v = er ? low_of<T>(b[pi] * pow2(-er[pi])) : low_of<T>(b[pi]);
     }
     xr[s] = v;
   }
@@ -1225,7 +1475,7 @@ __device__ void warp_lu_solve_s(const T* A, int N, const int* perm, const T* inv
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int i = lane + 32 * s;
-    if (i < N) x[i] = ec ? (double)xr[s] * pow2(-ec[i]) : (double)xr[s];
+    if (i < N) x[i] = ec ? high_of(xr[s]) * pow2(-ec[i]) : high_of(xr[s]);
   }
   __syncwarp();
 }

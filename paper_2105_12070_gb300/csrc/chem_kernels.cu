@@ -171,7 +171,7 @@ __host__ __device__ inline int lu_probe_doubles(int N, int bytes) {
 }
 
 template <typename S>
-__global__ void __launch_bounds__(64) lu_probe_kernel(const double* A, int N, int64_t n, int blocked, S* F, S* D,
+__global__ void __launch_bounds__(64) lu_probe_kernel(const double* A, int N, int64_t n, int variant, S* F, S* D,
                                                       int32_t* P, int32_t* sing) {
   extern __shared__ double smem[];
   Grp<2> g;
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(64) lu_probe_kernel(const double* A, int N, in
     const double* Am = A + (size_t)m * N * N;
     for (int e = g.t; e < N * N; e += 64) to_factor(Am[e], a[e]);
     g.sync();
-    const bool ok = blocked ? cell_lu_blocked<2, S>(g, a, N, piv, perm, invd) : cell_lu<2, S>(g, a, N, piv, perm, invd);
+    const bool ok = cell_lu_any<2, S>(g, a, N, piv, perm, invd, variant);
     for (int e = g.t; e < N * N; e += 64) F[(size_t)m * N * N + e] = a[e];
     for (int i = g.t; i < N; i += 64) {
       D[(size_t)m * N + i] = invd[i];
@@ -245,6 +245,7 @@ struct chem_mech {
   HostMech host;
   DevMech dev;
   GraphCache graph;
+  cudaEvent_t ev[2] = {nullptr, nullptr};  // brackets the integrate launches when stats are asked for
   void* dbuf = nullptr;
   int device = 0;
   int num_sms = 0;
@@ -644,6 +645,8 @@ void chem_free_mechanism(chem_mech* m) {
   if (!m) return;
   if (m->graph.exec) cudaGraphExecDestroy(m->graph.exec);
   if (m->graph.capture_stream) cudaStreamDestroy(m->graph.capture_stream);
+  for (cudaEvent_t e : m->ev)
+    if (e) cudaEventDestroy(e);
   cudaFree(m->dbuf);
   cudaFree(m->d_totals);
   cudaFree(m->d_queue);
@@ -660,6 +663,13 @@ int chem_mech_dims(const chem_mech* m, int* K, int* R) {
   if (!m) return set_err(CHEM_EINVAL, "chem_mech_dims: NULL mechanism");
   if (K) *K = m->host.K;
   if (R) *R = m->host.R;
+  return CHEM_OK;
+}
+
+int chem_mech_counts(const chem_mech* m, int* n_third_body, int* n_falloff) {
+  if (!m) return set_err(CHEM_EINVAL, "chem_mech_counts: NULL mechanism");
+  if (n_third_body) *n_third_body = m->host.n_tb;
+  if (n_falloff) *n_falloff = m->host.n_fo;
   return CHEM_OK;
 }
 
@@ -788,12 +798,18 @@ static int integrate_impl(const chem_mech* mc, double p_Pa, double* T, double* Y
   a.solver = o.solver;
   a.fdjac = o.jacobian == CHEM_JAC_FD;
   a.p_cells = p_cells;
-  if (o.use_graph && dev) {
+  if (stats) {
+    for (cudaEvent_t& e : m->ev)
+      if (!e) CK(cudaEventCreate(&e));
+    CK(cudaEventRecord(m->ev[0], st));
+  }
+  if (o.use_graph) {
     rc = launch_via_graph(m, o, a, st);
   } else {
     rc = enqueue_integrate(m, o, a, st);
   }
   if (rc) return rc;
+  if (stats) CK(cudaEventRecord(m->ev[1], st));
   if (!dev) {
     CK(cudaMemcpyAsync(T, dT, sizeof(double) * ncells, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(Y, dY, sizeof(double) * K * ncells, cudaMemcpyDeviceToHost, st));
@@ -808,6 +824,9 @@ static int integrate_impl(const chem_mech* mc, double p_Pa, double* T, double* Y
     stats->rejects = (int64_t)tot[1];
     stats->failed_cells = (int64_t)tot[2];
     stats->refine_fallbacks = (int64_t)tot[3];
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, m->ev[0], m->ev[1]));
+    stats->kernel_ms = ms;
   } else if (!dev) {
     CK(cudaStreamSynchronize(st));
   }
@@ -1111,11 +1130,12 @@ int chem_debug_exp(const double* x, double* y, int64_t n, void* stream) {
   return CHEM_OK;
 }
 
-int chem_debug_lu(const double* A, int N, int64_t n, int precision, int blocked, void* factors, void* invdiag,
+int chem_debug_lu(const double* A, int N, int64_t n, int precision, int variant, void* factors, void* invdiag,
                   int32_t* perm, int32_t* singular, void* stream) {
   if (N < 1 || N > 128 || n < 0) return set_err(CHEM_EINVAL, "chem_debug_lu: need 1 <= N <= 128 and n >= 0");
   if (precision != CHEM_PREC_FP64 && precision != CHEM_PREC_MIXED && precision != CHEM_PREC_MIXED_FF)
     return set_err(CHEM_EINVAL, "chem_debug_lu: unknown precision");
+  if (variant < 0 || variant > 2) return set_err(CHEM_EINVAL, "chem_debug_lu: variant must be 0, 1 or 2");
   if (n == 0) return CHEM_OK;
   if (!is_device_ptr(A) || !is_device_ptr(factors) || !is_device_ptr(invdiag) || !is_device_ptr(perm) ||
       !is_device_ptr(singular))
@@ -1126,15 +1146,15 @@ int chem_debug_lu(const double* A, int N, int64_t n, int precision, int blocked,
   const size_t smem = sizeof(double) * (size_t)lu_probe_doubles(N, bytes);
   if (precision == CHEM_PREC_FP64) {
     CK(cudaFuncSetAttribute(lu_probe_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    lu_probe_kernel<double><<<grid, 64, smem, st>>>(A, N, n, blocked, static_cast<double*>(factors),
+    lu_probe_kernel<double><<<grid, 64, smem, st>>>(A, N, n, variant, static_cast<double*>(factors),
                                                     static_cast<double*>(invdiag), perm, singular);
   } else if (precision == CHEM_PREC_MIXED) {
     CK(cudaFuncSetAttribute(lu_probe_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    lu_probe_kernel<float><<<grid, 64, smem, st>>>(A, N, n, blocked, static_cast<float*>(factors),
+    lu_probe_kernel<float><<<grid, 64, smem, st>>>(A, N, n, variant, static_cast<float*>(factors),
                                                    static_cast<float*>(invdiag), perm, singular);
   } else {
     CK(cudaFuncSetAttribute(lu_probe_kernel<FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    lu_probe_kernel<FF><<<grid, 64, smem, st>>>(A, N, n, blocked, static_cast<FF*>(factors),
+    lu_probe_kernel<FF><<<grid, 64, smem, st>>>(A, N, n, variant, static_cast<FF*>(factors),
                                                 static_cast<FF*>(invdiag), perm, singular);
   }
   CK(cudaGetLastError());

@@ -66,6 +66,12 @@ __device__ void cell_fd_jacobian(const DevMech& m, const Grp<G>& g, double p, co
 #define CHEM_MIXED_FP64_RUN 16
 #endif
 
+// Refinement stops when the last correction is below this fraction of the error-control scale
+// atol + rtol |y| of every component (or the residual is at the FP64 rounding level)
+#ifndef CHEM_REFINE_TOL
+#define CHEM_REFINE_TOL 1e-5
+#endif
+
 // v 2^k for a power-of-two scaling whose result is at most 2 (an exponent-field add, no FP64
 // operation); zero when v is zero or subnormal or the result would be subnormal.
 __device__ inline double scale2(double v, int k) {
@@ -78,7 +84,7 @@ __device__ inline double scale2(double v, int k) {
 template <typename L>
 __device__ inline L to_low(double v);
 template <>
-__device__ inline float to_low<float>(double v) { return __double2float_rn(v); }
+__device__ inline float to_low<float>(double v) { return f32_of(v); }
 template <>
 __device__ inline FF to_low<FF>(double v) { return FF(v); }
 
@@ -113,7 +119,7 @@ __device__ bool form_and_factor_low(const Grp<G>& g, const CellMem& w, int N, do
     S[e] = to_low<L>(scale2(i == j ? dg[i] : w.A[e], -w.er[i] - w.ec[j]));
   }
   g.sync();
-  return cell_lu_blocked<G, L>(g, S, N, w.piv, w.perm, invd);
+  return cell_lu_default<G, L>(g, S, N, w.piv, w.perm, invd);
 }
 
 // x <- W^-1 b through the low-precision factors of the equilibrated matrix S = D_r W D_c:
@@ -171,13 +177,13 @@ __device__ bool stage_solve_low(const Grp<G>& g, const CellMem& w, const Integra
     for (int i = g.t; i < N; i += NT) {
       const double d = w.res[i];
       u[i] += d;
-      c = Grp<G>::nanmax(c, fabs(d) / (a.atol + a.rtol * fabs(w.y[i])));
+      c = Grp<G>::nanmax(c, fabs(d) * w.err[i]);  // w.err: 1 / (atol + rtol |y|), set per attempt
     }
     conv = g.max_nan_any(c, above);
     if (!above && conv == conv) conv = 0.0;  // residual at the FP64 rounding level
-    if (conv <= 1e-5) break;
+    if (conv <= CHEM_REFINE_TOL) break;
   }
-  return conv <= 1e-5;
+  return conv <= CHEM_REFINE_TOL;
 }
 
 // u <- W^-1 rhs: FP64 factors (lowp 0: one solve), FP32 factors (1) or FP32 pairs (2).
@@ -271,6 +277,11 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) integrate_kernel(
       for (int pass = (a.mixed && attempt >= f64_until) ? 0 : 1; pass < 2; ++pass) {
         const int lowp = pass == 0 ? a.mixed : 0;
         bool ok;
+        if (lowp) {
+          // reciprocal error-control scales of the refinement's stopping test (the error vector is
+          // free until the stages are combined)
+          for (int i = g.t; i < N; i += NT) w.err[i] = 1.0 / (a.atol + a.rtol * fabs(w.y[i]));
+        }
         if (lowp == 1) {
           ok = form_and_factor_low<G, float>(g, w, N, gh, w.invd32);
         } else if (lowp == 2) {
@@ -280,11 +291,7 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) integrate_kernel(
           g.sync();
           for (int i = g.t; i < N; i += NT) w.B[i * N + i] += gh;
           g.sync();
-#ifdef CHEM_LU_BLOCKED_FP64
-          ok = cell_lu_blocked<G, double>(g, w.B, N, w.piv, w.perm, w.invdiag);
-#else
-          ok = cell_lu<G, double>(g, w.B, N, w.piv, w.perm, w.invdiag);
-#endif
+          ok = cell_lu_default<G, double>(g, w.B, N, w.piv, w.perm, w.invdiag);
         }
         PHASE_END(2);
         if (!ok) break;  // exactly singular: reject the attempt
@@ -355,6 +362,15 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) integrate_kernel(
         err = g.max_nan(e);
         break;
       }
+      // err^(-1/4) of the step-size factor, by one thread for the group (see cell_rates)
+      double p25;
+      if (G > 1) {
+        if (g.t == 0) w.bc[5] = pow(err, -0.25);
+        g.sync();
+        p25 = w.bc[5];
+      } else {
+        p25 = pow(err, -0.25);
+      }
       double fac;
       if (err <= 1.0) {
         if (a.rec) {
@@ -369,14 +385,14 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) integrate_kernel(
         g.sync();
         ++nsteps;
         need_jac = true;
-        fac = fmin(6.0, fmax(0.2, 0.9 * pow(err, -0.25)));
+        fac = fmin(6.0, fmax(0.2, 0.9 * p25));
         if (last_rej) fac = fmin(fac, 1.0);
         last_rej = false;
         h_next = h * fac;
         if (t >= a.dt) break;
       } else {
         ++nrej;
-        fac = (err == err && err < INFINITY) ? fmax(0.2, 0.9 * pow(err, -0.25)) : 0.2;
+        fac = (err == err && err < INFINITY) ? fmax(0.2, 0.9 * p25) : 0.2;
         fac = fmin(fac, 1.0);
         last_rej = true;
         h_next = h * fac;
@@ -487,7 +503,7 @@ __global__ void __launch_bounds__(CHEM_MAX_THREADS_PER_CTA, 1) seulex_kernel(Dev
         g.sync();
         for (int i = g.t; i < N; i += NT) w.B[i * N + i] += gh;
         g.sync();
-        if (!cell_lu<G, double>(g, w.B, N, w.piv, w.perm, w.invdiag)) { badstep = true; break; }
+        if (!cell_lu_default<G, double>(g, w.B, N, w.piv, w.perm, w.invdiag)) { badstep = true; break; }
         for (int i = g.t; i < N; i += NT) yi[i] = w.y[i];
         for (int sub = 0; sub < j; ++sub) {
           const double* fsrc = w.f0;

@@ -7,7 +7,10 @@ cell group for: the rate evaluation with Jacobian data, the Jacobian assembly, W
 stage solves (with any refinement), the two stage rate evaluations and the step control.  The
 timers perturb the kernel a little; compare phases, not absolute speed.
 
-    python -m paper_2105_12070_gb300.phases [--cells 1216] [--dt 1e-8]
+    python -m paper_2105_12070_gb300.phases [--cells 1216] [--dt 1e-8] [--define NAME ...] [--modes 0,2]
+
+--define adds a preprocessor macro to the timer build (e.g. CHEM_LU_VARIANT=0: the LU column by
+column, =2: in 8-column panels; CHEM_LU_RCP_DIVISION: FP64 pivot reciprocals by division).
 """
 from __future__ import annotations
 
@@ -26,11 +29,14 @@ def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--cells", type=int, default=1216)
     ap.add_argument("--dt", type=float, default=1e-8)
+    ap.add_argument("--define", action="append", default=[], help="extra macro of the timer build")
+    ap.add_argument("--modes", default="", help="comma-separated indices into MODES (default: all)")
     args = ap.parse_args(argv)
 
     from . import build
-    out = os.path.join(build.BUILD, "phase_timers", "libchemgpu.so")
-    build.build(defines=["CHEM_PHASE_TIMERS"], out=out, force=True)
+    tag = "_".join(["phase_timers"] + [d.lower().replace("=", "") for d in args.define])
+    out = os.path.join(build.BUILD, tag, "libchemgpu.so")
+    build.build(defines=["CHEM_PHASE_TIMERS"] + list(args.define), out=out, force=True)
     build.LIB = out  # this process loads the timer build
     import torch
 
@@ -42,7 +48,9 @@ def main(argv=None) -> int:
     n = min(args.cells, w["T"].shape[0])
     idx = np.arange(n) * (w["T"].shape[0] // n)
     buf = (ctypes.c_ulonglong * 8)()
-    for prec, sweeps in MODES:
+    modes = [MODES[int(i)] for i in args.modes.split(",")] if args.modes else MODES
+    print("defines: " + (" ".join(args.define) or "(none)"), flush=True)
+    for prec, sweeps in modes:
         T = torch.from_numpy(w["T"][idx].copy()).cuda()
         Y = torch.from_numpy(w["Y"][:, idx].copy()).cuda()
         opts = chem.default_opts(warps_per_cell=2, precision=prec, refine_sweeps=sweeps)

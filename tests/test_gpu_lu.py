@@ -1,7 +1,7 @@
 """The kernels' dense LU with partial pivoting (Sec. 2.3: dense LU + back substitution), through
-chem_debug_lu: the panel-blocked factorisation gives bitwise the factors of the column-by-column
-one in every factor precision (the same pivots and the same operations on every entry, in the
-same order), and the FP64 factors equal LAPACK's (scipy.linalg.lu_factor, whose pivot is also the
+chem_debug_lu: its schedule with two barriers per column (the integrate kernels' default) and its
+panel-blocked schedule give bitwise the factors of the column-by-column one in every factor
+precision (the same pivots and the same operations on every entry, in the same order), and the FP64 factors equal LAPACK's (scipy.linalg.lu_factor, whose pivot is also the
 first largest |a|) on random matrices, with reciprocal pivots within one unit in the last place.
 """
 import numpy as np
@@ -30,15 +30,16 @@ def _matrices(N, n, seed):
     return A
 
 
-@pytest.mark.parametrize("N", [1, 5, 8, 9, 16, 31, 53, 100, 128])
+@pytest.mark.parametrize("N", [1, 2, 5, 8, 9, 16, 31, 32, 33, 53, 64, 65, 100, 128])
 @pytest.mark.parametrize("prec", PRECISIONS)
-def test_blocked_lu_bitwise_equal(N, prec):
+@pytest.mark.parametrize("variant", [1, 2])
+def test_lu_schedules_bitwise_equal(N, prec, variant):
     A = torch.from_numpy(_matrices(N, 24, 1000 + N)).cuda()
-    ref = chem.chem_debug_lu(A, prec, blocked=False)
-    out = chem.chem_debug_lu(A, prec, blocked=True)
+    ref = chem.chem_debug_lu(A, prec, variant=0)
+    out = chem.chem_debug_lu(A, prec, variant=variant)
     torch.cuda.synchronize()
     for r, o in zip(ref, out):
-        assert torch.equal(r.view(torch.int32), o.view(torch.int32)), (N, prec)
+        assert torch.equal(r.view(torch.int32), o.view(torch.int32)), (N, prec, variant)
 
 
 @pytest.mark.parametrize("N", [5, 53, 100])
@@ -46,7 +47,7 @@ def test_fp64_lu_matches_lapack(N):
     scipy_linalg = pytest.importorskip("scipy.linalg")
     A = _matrices(N, 12, 2000 + N)[: 2 * 12 // 3]  # no tied columns: pivots are unique
     F, D, P, S = (t.cpu().numpy() for t in chem.chem_debug_lu(torch.from_numpy(A).cuda(), chem.CHEM_PREC_FP64,
-                                                               blocked=True))
+                                                               variant=1))
     for m in range(A.shape[0]):
         lu, piv = scipy_linalg.lu_factor(A[m])
         perm = np.arange(N)
@@ -66,6 +67,6 @@ def test_singular_flag():
     N = 20
     A = np.random.default_rng(3).normal(size=(2, N, N))
     A[1][:, 7] = 0.0  # an exactly zero column
-    for blocked in (False, True):
-        *_, S = chem.chem_debug_lu(torch.from_numpy(A).cuda(), chem.CHEM_PREC_FP64, blocked=blocked)
+    for variant in (0, 1, 2):
+        *_, S = chem.chem_debug_lu(torch.from_numpy(A).cuda(), chem.CHEM_PREC_FP64, variant=variant)
         assert S.cpu().tolist() == [0, 1]

@@ -5,7 +5,9 @@ Tolerances (stated from the arithmetic):
     |forward| + |reverse| fluxes that enter it).  Both sides round exp() of arguments up to a
     few hundred and sum in different orders, so the error is a few 1e-14 of the gross flux;
     near partial equilibrium the net rate can be many orders below the gross scale.
-  * Jacobian: |J_gpu - J_oracle| <= 1e-11 * max_j |J_oracle(i, j)| per row (row-normwise).
+  * Jacobian: |J_gpu - J_oracle| <= 1e-12 * max_j |J_oracle(i, j)| per row (row-normwise), the
+    stated gate for Jacobian entries.
+  Both tests print the measured maximum (and 99th percentile) of their error measure.
   * integrate: |x_gpu - x_oracle| <= 1e-6 |x_oracle| + 1e-10 for T and every Y (rtol/atol-shaped),
     the same adaptive method and controller on both sides.
 """
@@ -81,7 +83,9 @@ def test_rates_parity(which, request):
     f = _gpu_rates(mech, w["p_Pa"], T, Y)
     fo, gross = ora.rates(w["p_Pa"], T, Y, gross=True)
     err = np.abs(f - fo)
-    assert np.all(err <= 1e-11 * gross + 1e-300), (err / gross).max()
+    rel = err / np.maximum(gross, 1e-300)
+    print(f"rates parity {which}: max |f_gpu - f_oracle| / gross {rel.max():.3e}, p99 {np.percentile(rel, 99):.3e}")
+    assert np.all(err <= 1e-11 * gross + 1e-300), rel.max()
 
 
 @pytest.mark.parametrize("which", ["small", "shear"])
@@ -93,7 +97,10 @@ def test_jacobian_parity(which, request):
     Jo = ora.jacobian(w["p_Pa"], T, Y)
     rowmax = np.abs(Jo).max(axis=2, keepdims=True)
     rel = np.abs(J - Jo) / rowmax
-    assert rel.max() < 1e-11, rel.max()
+    worst = np.unravel_index(np.argmax(rel), rel.shape)
+    print(f"jacobian parity {which}: max row-normwise {rel.max():.3e} (cell {worst[0]}, row {worst[1]}), "
+          f"p99 {np.percentile(rel, 99):.3e}")
+    assert rel.max() <= 1e-12, rel.max()
 
 
 def _assert_state_close(T, Y, To, Yo):
