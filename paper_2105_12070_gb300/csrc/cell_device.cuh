@@ -388,7 +388,9 @@ __device__ const double c_exp2_j32[64] = {
     0x1.f50765b6e4540p+0, 0x1.9d3e12dd8a18bp-54};
 
 __device__ inline double exp_fast(double x) {
-  if (!(fabs(x) < 708.0)) return exp(x);
+  // |x| < 708 by an integer compare of the bit pattern with the sign masked (monotone for
+  // non-negative doubles; NaN compares above), so the range check costs no FP64 instruction
+  if ((__double_as_longlong(x) & 0x7fffffffffffffffLL) >= 0x4086200000000000LL) return exp(x);
   const double shifter = 0x1.8p52;  // adding it rounds x 32/ln2 to an integer in the low bits
   const double t = fma(x, 0x1.71547652b82fep+5, shifter);
   const int k = (int)__double2loint(t);
@@ -536,7 +538,18 @@ __device__ CellScalarsT<S> cell_rates(const DevMech& m, const Grp<G>& g, double 
   }
   g.sync();
   const S ln_patm_rut = kLnPatmRu - s.lnT;  // ln(Patm / (Ru T))
-  for (int r = g.t; r < m.R; r += NT) {
+  // reactions: warp 0 takes [0, split) (the fall-off reactions, whose Troe branch is long, lead
+  // the device order), the other warps [split, R); the split balances the warps' iteration costs
+  // (split 0: reaction r goes to thread r mod 32 G)
+#ifdef CHEM_RX_INTERLEAVED
+  const int split = 0;
+#else
+  const int split = (G == 1) ? 0 : m.rx_split[G == 2 ? 1 : G == 4 ? 2 : 3];
+#endif
+  const int r_first = (split == 0) ? g.t : (g.warp() == 0) ? g.lane() : split + g.t - 32;
+  const int r_end = (split == 0 || g.warp() != 0) ? m.R : split;
+  const int r_step = (split == 0) ? NT : (g.warp() == 0) ? 32 : NT - 32;
+  for (int r = r_first; r < r_end; r += r_step) {
     const int* ii = m.rxi + r * kRxInts;
     const double* rd = m.rxd + r * kRxDoubles;
     const int a0 = ii[0], a1 = ii[1], p0 = ii[2], p1 = ii[3];
@@ -646,12 +659,30 @@ __device__ void cell_jacobian(const DevMech& m, const Grp<G>& g, const CellScala
   for (int e = g.t; e < N * N; e += NT) Z[e] = cst<S>(0.0);
   g.sync();
   // mass-action part: one thread per receiving Z entry sums its contributions (a fixed plan
-  // built with the mechanism; no two threads write the same entry, no atomics)
-  for (int e = g.t; e < m.zg_entries; e += NT) {
-    S acc = cst<S>(0.0);
-    const int cb = m.zg_ptr[e], ce = m.zg_ptr[e + 1];
-    for (int c = cb; c < ce; ++c) acc = fma(m.zg_coef[c], scr[m.zg_src[c]], acc);
-    Z[m.zg_dst[e]] = acc;
+  // built with the mechanism; no two threads write the same entry, no atomics).  Each thread
+  // takes four entries at once, NT apart, so that four independent FMA chains hide each other's
+  // FP64 latency; every entry still sums its contributions in plan order.
+  for (int e0 = g.t; e0 < m.zg_entries; e0 += 4 * NT) {
+    int cb[4], len[4];
+    S acc[4];
+    int lmax = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = e0 + q * NT;
+      const bool ok = e < m.zg_entries;
+      cb[q] = ok ? m.zg_ptr[e] : 0;
+      len[q] = ok ? m.zg_ptr[e + 1] - cb[q] : 0;
+      lmax = max(lmax, len[q]);
+      acc[q] = cst<S>(0.0);
+    }
+    for (int c = 0; c < lmax; ++c) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c < len[q]) acc[q] = fma(m.zg_coef[cb[q] + c], scr[m.zg_src[cb[q] + c]], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (e0 + q * NT < m.zg_entries) Z[m.zg_dst[e0 + q * NT]] = acc[q];
   }
   g.sync();
   // efficiency part of the pressure-dependent reactions: Z[k][j] += sum_r v_kr eff_rj over the
@@ -661,14 +692,35 @@ __device__ void cell_jacobian(const DevMech& m, const Grp<G>& g, const CellScala
   for (int c = g.t; c < m.n_pairs; c += NT) v[c] = m.pr_nu[c] * scr[4 * m.R + m.pr_pd[c]];
   g.sync();
   {
+    // four (row, column) items per thread at once, NT apart (independent FMA chains); each item
+    // sums its row's pairs in plan order
     const float invK = 1.0f / (float)K;
     const int items = m.n_prows * K;
-    for (int x = g.t; x < items; x += NT) {
-      const int ri = (int)(((float)x + 0.5f) * invK), j = x - ri * K;
-      const int row = m.pr_rows[ri];
-      S acc = cst<S>(0.0);
-      for (int c = m.pr_ptr[row]; c < m.pr_ptr[row + 1]; ++c) acc = fma(v[c], m.eff[(size_t)m.pr_pd[c] * K + j], acc);
-      Z[row * N + j] += acc;
+    for (int x0 = g.t; x0 < items; x0 += 4 * NT) {
+      int zi[4], jj[4], cb[4], len[4];
+      S acc[4];
+      int lmax = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int x = x0 + q * NT;
+        const bool ok = x < items;
+        const int ri = ok ? (int)(((float)x + 0.5f) * invK) : 0;
+        jj[q] = ok ? x - ri * K : 0;
+        const int row = m.pr_rows[ri];
+        zi[q] = row * N + jj[q];
+        cb[q] = m.pr_ptr[row];
+        len[q] = ok ? m.pr_ptr[row + 1] - cb[q] : 0;
+        lmax = max(lmax, len[q]);
+        acc[q] = cst<S>(0.0);
+      }
+      for (int c = 0; c < lmax; ++c) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (c < len[q]) acc[q] = fma(v[cb[q] + c], m.eff[(size_t)m.pr_pd[cb[q] + c] * K + jj[q]], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (x0 + q * NT < items) Z[zi[q]] += acc[q];
     }
   }
   g.sync();
@@ -738,7 +790,19 @@ __device__ void cell_jacobian(const DevMech& m, const Grp<G>& g, const CellScala
   if (g.t == 0) J[0] = (cpw + dqt - zqc * s.invT) * inv_rhocp + fT * (-s.invT + s.dcp_dT * inv_cp);
   const int nb = d * d;
   const float inv_d = 1.0f / (float)d;
-  for (int e = g.t; e < nb; e += NT) {
+  // two entries per thread and iteration (independent chains), the same operations per entry
+  int e = g.t;
+  for (; e + NT < nb; e += 2 * NT) {
+    const int k0 = (int)(((float)e + 0.5f) * inv_d), i0 = e - k0 * d;
+    const int k1 = (int)(((float)(e + NT) + 0.5f) * inv_d), i1 = e + NT - k1 * d;
+    const double W0 = m.sp[k0 * kSpDoubles], iW0 = m.sp[i0 * kSpDoubles + 1];
+    const double W1 = m.sp[k1 * kSpDoubles], iW1 = m.sp[i1 * kSpDoubles + 1];
+    const S j0 = fma(-w.rowB[k0], w.ccol[i0], fma(-W0 * iW0, Z[k0 * N + i0], w.rowA[k0]));
+    const S j1 = fma(-w.rowB[k1], w.ccol[i1], fma(-W1 * iW1, Z[k1 * N + i1], w.rowA[k1]));
+    J[(1 + k0) * N + 1 + i0] = j0;
+    J[(1 + k1) * N + 1 + i1] = j1;
+  }
+  if (e < nb) {
     const int k = (int)(((float)e + 0.5f) * inv_d), i = e - k * d;
     const double Wk = m.sp[k * kSpDoubles];
     const double invWi = m.sp[i * kSpDoubles + 1];

@@ -92,6 +92,9 @@ struct DevMech {
   const int* pr_row;
   const int* pr_rows;
   int n_pairs, n_prows;
+  // reaction split of the rate evaluation for groups of 2, 4 and 8 warps (index 1, 2, 3; index 0
+  // unused): warp 0 takes reactions [0, split), the other warps [split, R); 0 = interleaved
+  int rx_split[4];
   const int* order;  // device reaction index -> file reaction index
   const int* cl_ptr;
   const int* cl_src;

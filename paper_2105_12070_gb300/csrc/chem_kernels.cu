@@ -280,6 +280,41 @@ int set_err(int code, const std::string& msg) {
     if (e_ != cudaSuccess) return set_err(CHEM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+// Reaction split of cell_rates for a group of G warps.  The fall-off reactions come first in
+// device order (Troe, then Lindemann), and a warp iteration that holds a Troe reaction costs about
+// six plain ones (measured with clock64() per warp on the 53-species mechanism: 39 k against
+// 6.1 k cycles; three more exponentials, two logarithms and five quotients), so interleaving the
+// reactions over all warps leaves warp 0 with the slowest iterations while the others wait at the
+// next barrier.  Warp 0 takes reactions [0, a) and the other G - 1 warps [a, R), with a a multiple
+// of 32, at least the fall-off count, that minimises the larger side's cost (a warp iteration
+// costing 6 with a Troe reaction, 2 with a Lindemann one, else 1).  If the plain interleaving
+// (reaction r to thread r mod 32 G) costs no more, the split is 0, which keeps it.
+int reaction_split(int R, int n_troe, int n_fo, int G) {
+  if (G <= 1) return R;
+  auto iter_cost = [&](int s) { return (s < n_troe) ? 6 : (s < n_fo) ? 2 : 1; };
+  int inter = 0;
+  for (int w = 0; w < G; ++w) {
+    int c = 0;
+    for (int s = 32 * w; s < R; s += 32 * G) c += iter_cost(s);
+    inter = std::max(inter, c);
+  }
+  const int top = (R + 31) / 32 * 32;
+  int best_a = 0, best = inter;
+  for (int a = 32; a <= top; a += 32) {
+    if (a < n_fo) continue;
+    int c0 = 0;
+    for (int s = 0; s < a && s < R; s += 32) c0 += iter_cost(s);
+    const int rest = std::max(0, R - a);
+    const int c1 = (rest + 32 * (G - 1) - 1) / (32 * (G - 1));
+    const int c = std::max(c0, c1);
+    if (c < best) {
+      best = c;
+      best_a = std::min(a, R);
+    }
+  }
+  return best_a;
+}
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes at;
@@ -629,6 +664,12 @@ int chem_load_mechanism(const char* path, chem_mech** out) {
   d.cl_rx = reinterpret_cast<const int*>(b + o_clr);
   d.n_pairs = (int)h.pr_pd.size();
   d.n_prows = (int)h.pr_rows.size();
+  {
+    int n_troe = 0;
+    for (int r = 0; r < h.n_fo; ++r) n_troe += h.fo[(size_t)r * kFoDoubles + 7] != 0.0;
+    d.rx_split[0] = h.R;
+    for (int i = 1; i < 4; ++i) d.rx_split[i] = reaction_split(h.R, n_troe, h.n_fo, 1 << i);
+  }
   if (d.n_pairs > 8 * (((h.K + 1) / 2) * 2)) {
     chem_free_mechanism(m);
     return set_err(CHEM_ESIZE, "chem_load_mechanism: too many pressure-dependent (row, reaction) pairs");
