@@ -527,14 +527,17 @@ __device__ CellScalarsT<S> cell_rates(const DevMech& m, const Grp<G>& g, double 
   // third-body concentrations [M]_r = sum_k eff_rk C_k of the pressure-dependent reactions
   for (int r = g.t; r < m.n_pd; r += NT) {
     const double* e = m.eff + (size_t)r * K;
-    S a0 = cst<S>(0.0), a1 = cst<S>(0.0);
+    // four partial sums: independent FMA chains a quarter as long
+    S a0 = cst<S>(0.0), a1 = cst<S>(0.0), a2 = cst<S>(0.0), a3 = cst<S>(0.0);
     int k = 0;
-    for (; k + 1 < K; k += 2) {
+    for (; k + 3 < K; k += 4) {
       a0 = fma(e[k], w.C[k], a0);
       a1 = fma(e[k + 1], w.C[k + 1], a1);
+      a2 = fma(e[k + 2], w.C[k + 2], a2);
+      a3 = fma(e[k + 3], w.C[k + 3], a3);
     }
-    if (k < K) a0 = fma(e[k], w.C[k], a0);
-    w.M[r] = a0 + a1;
+    for (; k < K; ++k) a0 = fma(e[k], w.C[k], a0);
+    w.M[r] = (a0 + a1) + (a2 + a3);
   }
   g.sync();
   const S ln_patm_rut = kLnPatmRu - s.lnT;  // ln(Patm / (Ru T))
@@ -633,8 +636,16 @@ __device__ CellScalarsT<S> cell_rates(const DevMech& m, const Grp<G>& g, double 
   // species production rates and the source term
   S Qp = cst<S>(0.0);
   for (int k = g.t; k < K; k += NT) {
-    S om = cst<S>(0.0);
-    for (int e = m.sr_ptr[k]; e < m.sr_ptr[k + 1]; ++e) om = fma(m.sr_nu[e], w.q[m.sr_idx[e]], om);
+    // two partial sums (independent FMA chains) over the species' reactions
+    S om0 = cst<S>(0.0), om1 = cst<S>(0.0);
+    const int eb = m.sr_ptr[k], ee = m.sr_ptr[k + 1];
+    int e = eb;
+    for (; e + 1 < ee; e += 2) {
+      om0 = fma(m.sr_nu[e], w.q[m.sr_idx[e]], om0);
+      om1 = fma(m.sr_nu[e + 1], w.q[m.sr_idx[e + 1]], om1);
+    }
+    if (e < ee) om0 = fma(m.sr_nu[e], w.q[m.sr_idx[e]], om0);
+    const S om = om0 + om1;
     w.omega[k] = om;
     Qp = fma(w.hRT[k], om, Qp);
     if (k < d) f[1 + k] = m.sp[k * kSpDoubles] * om * s.inv_rho;
@@ -729,15 +740,26 @@ __device__ void cell_jacobian(const DevMech& m, const Grp<G>& g, const CellScala
   const S RuT = kRu * s.T;
   S* wq = w.wq;
   for (int k = g.t; k < d; k += NT) {
-    S zc = cst<S>(0.0), dw = cst<S>(0.0);
-    for (int e = m.sr_ptr[k]; e < m.sr_ptr[k + 1]; ++e) {
+    // two partial sums each (four independent FMA chains)
+    S zc0 = cst<S>(0.0), dw0 = cst<S>(0.0), zc1 = cst<S>(0.0), dw1 = cst<S>(0.0);
+    const int eb = m.sr_ptr[k], ee = m.sr_ptr[k + 1];
+    int e = eb;
+    for (; e + 1 < ee; e += 2) {
+      const double nu0 = m.sr_nu[e], nu1 = m.sr_nu[e + 1];
+      const int r0 = m.sr_idx[e], r1 = m.sr_idx[e + 1];
+      zc0 = fma(nu0, scr[5 * m.R + r0], zc0);
+      dw0 = fma(nu0, scr[6 * m.R + r0], dw0);
+      zc1 = fma(nu1, scr[5 * m.R + r1], zc1);
+      dw1 = fma(nu1, scr[6 * m.R + r1], dw1);
+    }
+    if (e < ee) {
       const double nu = m.sr_nu[e];
       const int r = m.sr_idx[e];
-      zc = fma(nu, scr[5 * m.R + r], zc);
-      dw = fma(nu, scr[6 * m.R + r], dw);
+      zc0 = fma(nu, scr[5 * m.R + r], zc0);
+      dw0 = fma(nu, scr[6 * m.R + r], dw0);
     }
-    w.zc[k] = zc;
-    w.dwT[k] = dw;
+    w.zc[k] = zc0 + zc1;
+    w.dwT[k] = dw0 + dw1;
     // mass conservation (sum_k W_k omega_k = 0) gives omega_K = -sum_{k<K} (W_k/W_K) omega_k, so
     // Q = sum_k H_k omega_k = sum_{k<K} (H_k - H_K W_k/W_K) omega_k: the enthalpy row is a
     // weighted sum of the species rows
@@ -748,14 +770,16 @@ __device__ void cell_jacobian(const DevMech& m, const Grp<G>& g, const CellScala
   // dQ/dT|_C = sum_k wq_k dw_k/dT|_C
   S zqc = cst<S>(0.0), dqt = cst<S>(0.0), cpw = cst<S>(0.0);
   for (int j = g.t; j < K; j += NT) {
-    S a0 = cst<S>(0.0), a1 = cst<S>(0.0);
+    S a0 = cst<S>(0.0), a1 = cst<S>(0.0), a2 = cst<S>(0.0), a3 = cst<S>(0.0);
     int k = 0;
-    for (; k + 1 < d; k += 2) {
+    for (; k + 3 < d; k += 4) {
       a0 = fma(wq[k], Z[k * N + j], a0);
       a1 = fma(wq[k + 1], Z[(k + 1) * N + j], a1);
+      a2 = fma(wq[k + 2], Z[(k + 2) * N + j], a2);
+      a3 = fma(wq[k + 3], Z[(k + 3) * N + j], a3);
     }
-    if (k < d) a0 = fma(wq[k], Z[k * N + j], a0);
-    const S zq = a0 + a1;
+    for (; k < d; ++k) a0 = fma(wq[k], Z[k * N + j], a0);
+    const S zq = (a0 + a1) + (a2 + a3);
     Z[d * N + j] = zq;
     zqc = fma(zq, w.C[j], zqc);
     cpw = fma(w.cpR[j], w.omega[j], cpw);
