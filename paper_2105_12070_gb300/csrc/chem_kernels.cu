@@ -1,5 +1,7 @@
-// chemgpu kernels and C ABI (see include/chemgpu.h): the forward integrator, the one-shot
-// rate and Jacobian kernels, and the host side (mechanism upload, launch shapes, CUDA graphs).
+// chemgpu host side and C ABI (see include/chemgpu.h): mechanism upload, launch shapes, CUDA
+// graphs, the one-shot rate and Jacobian kernels, the mapping kernels and the probes.  The
+// integrate kernels themselves are in integrate_device.cuh, compiled once per cell-group width
+// (integrate_g*.cu).
 //
 // GPU design (GB300, sm_103a).  A group of G warps integrates one cell at a time; a CTA holds
 // several independent cell groups; a persistent grid pulls cells from a device work queue (one
