@@ -273,8 +273,10 @@ int chem_debug_exp(const double* x, double* y, int64_t n, void* stream);
  * warps per matrix: variant 0 column by column with four group barriers per column, 1 with two
  * (the pivot search of the next column fused into the trailing update; the integrate kernels'
  * default), 2 in panels of 8 columns.  All three give bitwise the same results.  Writes per matrix
- * the factors (N*N entries: the unit lower factor's multipliers below the diagonal, the upper
- * factor on and above it) to `factors` and the reciprocal pivots (N entries) to `invdiag`, both
+ * the factors of P A = L D U' (N*N entries: the unit lower factor L's multipliers below the
+ * diagonal, the pivots D on it, and above it the unit upper factor U' = D^-1 U, i.e. each row of
+ * the upper factor U right of the diagonal times the reciprocal of its pivot, rounded once) to
+ * `factors` and the reciprocal pivots (N entries) to `invdiag`, both
  * in the precision's storage (8 bytes per entry for doubles and pairs, 4 for floats), the row
  * permutation (N ints: row i of the factors is row perm[i] of the matrix) to `perm`, and 1 if a
  * pivot was exactly zero, else 0, to `singular` (n ints).  Device arrays, owned by the caller;

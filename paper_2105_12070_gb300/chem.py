@@ -392,7 +392,9 @@ def chem_debug_exp(x, out, stream=None):
 def chem_debug_lu(A, precision: int = CHEM_PREC_FP64, variant: int = 0, stream=None):
     """The kernels' LU with partial pivoting of each matrix of A (n, N, N) float64 (device tensor),
     in the factor precision of `precision`, in schedule `variant` (0 column by column, 1 with the
-    next pivot search fused into the update, 2 in panels of 8 columns), for the tests.  Returns (factors, invdiag, perm, singular): factors (n, N*N) and invdiag (n, N) in the
+    next pivot search fused into the update, 2 in panels of 8 columns), for the tests.  Returns
+    (factors, invdiag, perm, singular): factors of P A = L D U' (L's multipliers below the
+    diagonal, the pivots D on it, U' = D^-1 U above it) (n, N*N) and invdiag (n, N) in the
     precision's storage (float64; float32; FP32 pairs as (n, N*N, 2) / (n, N, 2) float32), perm
     (n, N) int32, singular (n,) int32."""
     import torch

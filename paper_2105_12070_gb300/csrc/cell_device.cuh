@@ -348,6 +348,45 @@ struct CellScalarsT {
 };
 using CellScalars = CellScalarsT<double>;
 
+// 1/a by Newton's iteration for the reciprocal, r <- r + r (1 - m r), on the significand m of a
+// (normalised to +-[1, 2) by replacing the exponent field): the seed is the FP32 approximate
+// reciprocal (rcp.approx) of m's leading 24 bits, relative error below 2^-21; two steps in FP64
+// square the error twice (below 2^-84, under the final rounding), so the result is within one
+// unit in the last place of 1/a.  The exponent is then restored by an integer subtraction.  Four
+// FP64 operations instead of a full division; zero, subnormal, very large, infinite and NaN
+// arguments take the division.
+__device__ inline double rcp_newton(double a) {
+  const long long b = __double_as_longlong(a);
+  const int ef = (int)((b >> 52) & 0x7ff);
+  if (ef < 3 || ef > 2044) return 1.0 / a;
+  const long long mb = (b & (long long)0x800fffffffffffffULL) | (1023LL << 52);
+  const double m = __longlong_as_double(mb);
+  const unsigned hi = (unsigned)((unsigned long long)b >> 32);
+  // m as a float: sign, exponent 127, the top 23 significand bits (truncated)
+  const float mf = __uint_as_float((hi & 0x80000000u) | 0x3f800000u | (unsigned)((b >> 29) & 0x7fffff));
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(mf));
+  // rf in +-[0.5, 1]: the same value as a double, by moving its fields
+  const unsigned fb = __float_as_uint(rf);
+  const long long rb = ((long long)(fb >> 31) << 63) | ((long long)(((fb >> 23) & 0xff) - 127 + 1023) << 52) |
+                       ((long long)(fb & 0x7fffff) << 29);
+  double r = __longlong_as_double(rb);
+  double e = fma(-m, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-m, r, 1.0);
+  r = fma(r, e, r);
+  // 1/a = r 2^-(ef - 1023); r's exponent field is 1022 or 1023, the result's stays in [1, 2043]
+  return __longlong_as_double(__double_as_longlong(r) - ((long long)(ef - 1023) << 52));
+}
+
+// 1/x for the scalar types of the rate code (the fall-off quotients): Newton's reciprocal, and for
+// a dual number (1/v, -d/v^2) from it.
+__device__ inline double recip(double x) { return rcp_newton(x); }
+__device__ inline Dual recip(Dual x) {
+  const double r = rcp_newton(x.v);
+  return Dual(r, -x.d * r * r);
+}
+
 // exp(x) for the rate constants: Tang's table-driven method (P. T. P. Tang, "Table-driven
 // implementation of the exponential function in IEEE floating-point arithmetic", ACM TOMS 15,
 // 1989): x = (32 m + j) ln2/32 + r with |r| <= ln2/64, exp(x) = 2^m 2^(j/32) (1 + p(r)), p the
@@ -429,26 +468,32 @@ __device__ inline void nasa7(const double* a, S T, S invT, S lnT, S& cpR, S& hRT
   dcpR = a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]));
 }
 
-// Troe broadening: F and d log10 F / d log10 Pr; with jac also d ln F / dT at fixed Pr.
+// Troe broadening: F and d log10 F / d log10 Pr; with jac also d ln F / dT at fixed Pr.  The
+// quotients share three reciprocals (of den, of g and, with jac, of Fcent ln 10, each by
+// Newton's iteration) and the table carries 1/T3 and 1/T1, so nothing is divided.
 template <class S>
 __device__ inline void troe(const double* fo, S T, S invT, S Pr, S& F, S& dlF, S& dlnF_dT, bool jac) {
-  const double a = fo[3], T3 = fo[4], T1 = fo[5], T2 = fo[6];
-  const S e3 = exp_fast(-T / T3), e1 = exp_fast(-T / T1), e2 = exp_fast(-T2 * invT);
+  const double a = fo[3], T2 = fo[6], iT3 = fo[8], iT1 = fo[9];
+  const S e3 = exp_fast(-T * iT3), e1 = exp_fast(-T * iT1), e2 = exp_fast(-T2 * invT);
   const S Fcent = (1.0 - a) * e3 + a * e1 + e2;
   const S L = log10(Fcent);
   const S c = -0.4 - 0.67 * L, n = 0.75 - 1.27 * L;
   const S x = log10(Pr);
-  const S den = n - 0.14 * (x + c);
-  const S f1 = (x + c) / den;
+  const S xc = x + c;
+  const S den = n - 0.14 * xc;
+  const S iden = recip(den);
+  const S f1 = xc * iden;
   const S g = 1.0 + f1 * f1;
-  F = exp_fast(2.302585092994045684 * (L / g));
-  dlF = -2.0 * L * f1 / (g * g) * (n / (den * den));
+  const S ig = recip(g);
+  F = exp_fast(2.302585092994045684 * (L * ig));
+  const S ig2 = ig * ig, iden2 = iden * iden;
+  dlF = -2.0 * L * f1 * ig2 * (n * iden2);
   dlnF_dT = cst<S>(0.0);
   if (jac) {
-    const S dFc = -(1.0 - a) / T3 * e3 - a / T1 * e1 + T2 * invT * invT * e2;
-    const S dL = dFc / (Fcent * 2.302585092994045684);
-    const S df1_dL = (-0.67 * den - (x + c) * (-1.27 + 0.14 * 0.67)) / (den * den);
-    const S dlog10F_dL = 1.0 / g - L * 2.0 * f1 / (g * g) * df1_dL;
+    const S dFc = -(1.0 - a) * iT3 * e3 - a * iT1 * e1 + T2 * invT * invT * e2;
+    const S dL = dFc * recip(Fcent * 2.302585092994045684);
+    const S df1_dL = (-0.67 * den - xc * (-1.27 + 0.14 * 0.67)) * iden2;
+    const S dlog10F_dL = ig - L * 2.0 * f1 * ig2 * df1_dL;
     dlnF_dT = 2.302585092994045684 * dlog10F_dL * dL;
   }
 }
@@ -559,7 +604,8 @@ __device__ CellScalarsT<S> cell_rates(const DevMech& m, const Grp<G>& g, double 
     const S Ca0 = w.C[a0], Ca1 = (a1 >= 0) ? w.C[a1] : cst<S>(1.0);
     const S Cp0 = w.C[p0], Cp1 = (p1 >= 0) ? w.C[p1] : cst<S>(1.0);
     const S pf = Ca0 * Ca1, pr = Cp0 * Cp1;
-    S kf = exp_fast(fma(rd[1], s.lnT, rd[0]) - rd[2] * s.invT);
+    const S lkinf = fma(rd[1], s.lnT, rd[0]) - rd[2] * s.invT;
+    S kf = exp_fast(lkinf);
     S dG = w.gRT[p0] - w.gRT[a0];
     if (p1 >= 0) dG += w.gRT[p1];
     if (a1 >= 0) dG -= w.gRT[a1];
@@ -568,16 +614,20 @@ __device__ CellScalarsT<S> cell_rates(const DevMech& m, const Grp<G>& g, double 
     const S invKc = exp_fast(dG - (double)dnu * ln_patm_rut);
     S mfac = cst<S>(1.0), Mr = cst<S>(0.0);
     S Pr = cst<S>(0.0), F = cst<S>(1.0), dlF = cst<S>(0.0), dlnF_dT = cst<S>(0.0), k0 = cst<S>(0.0);
+    S inv1p = cst<S>(1.0);
     const bool pd = r < m.n_pd;
     const bool fo = r < m.n_fo;
     const double* fop = nullptr;
     if (pd) Mr = w.M[r];
     if (fo) {
       fop = m.fo + (size_t)r * kFoDoubles;
-      k0 = exp_fast(fma(fop[1], s.lnT, fop[0]) - fop[2] * s.invT);
-      Pr = k0 * Mr / kf;
+      // k0 / k_inf as one exponential of the difference of the logarithms (no quotient)
+      const S ratio = exp_fast(fma(fop[1], s.lnT, fop[0]) - fop[2] * s.invT - lkinf);
+      k0 = ratio * kf;
+      Pr = ratio * Mr;
       if (fop[7] != 0.0) troe(fop, s.T, s.invT, Pr, F, dlF, dlnF_dT, jac);
-      kf = kf * Pr / (1.0 + Pr) * F;
+      inv1p = recip(1.0 + Pr);
+      kf = kf * Pr * inv1p * F;
     } else if (pd) {
       mfac = Mr;
     }
@@ -594,7 +644,6 @@ __device__ CellScalarsT<S> cell_rates(const DevMech& m, const Grp<G>& g, double 
       const S dlnkinf = (rd[1] + rd[2] * s.invT) * s.invT;
       S phi = cst<S>(0.0), dlnk = dlnkinf;
       if (fo) {
-        const S inv1p = 1.0 / (1.0 + Pr);
         const S dk_dM = k0 * F * inv1p * (inv1p + dlF);
         phi = dk_dM * (pf - invKc * pr);
         const S dlnk0 = (fop[1] + fop[2] * s.invT) * s.invT;
@@ -627,7 +676,7 @@ __device__ CellScalarsT<S> cell_rates(const DevMech& m, const Grp<G>& g, double 
           const int k = ii[8 + u];
           if (k >= 0) gw = fma(rd[3 + u] * m.sp[k * kSpDoubles], vP[1 + k], gw);
         }
-        const S dq = fo ? q * (Pr / (1.0 + Pr) - dlF) : q;
+        const S dq = fo ? q * (Pr * inv1p - dlF) : q;
         P[r] = dq * s.inv_rho * (gw - vP[0] * (o[7 * R] / s.cp));
       }
     }
@@ -1052,36 +1101,6 @@ __device__ inline double lu_carry(float a) { return f64_of(a); }
 __device__ inline double lu_carry(FF a) { return __hiloint2double(__float_as_int(a.hi), __float_as_int(a.lo)); }
 template <typename S>
 __device__ inline S lu_recip(double c);
-// 1/a by Newton's iteration for the reciprocal, r <- r + r (1 - m r), on the significand m of a
-// (normalised to +-[1, 2) by replacing the exponent field): the seed is the FP32 approximate
-// reciprocal (rcp.approx) of m's leading 24 bits, relative error below 2^-21; two steps in FP64
-// square the error twice (below 2^-84, under the final rounding), so the result is within one
-// unit in the last place of 1/a.  The exponent is then restored by an integer subtraction.  Four
-// FP64 operations instead of a full division; zero, subnormal, very large, infinite and NaN
-// arguments take the division.
-__device__ inline double rcp_newton(double a) {
-  const long long b = __double_as_longlong(a);
-  const int ef = (int)((b >> 52) & 0x7ff);
-  if (ef < 3 || ef > 2044) return 1.0 / a;
-  const long long mb = (b & (long long)0x800fffffffffffffULL) | (1023LL << 52);
-  const double m = __longlong_as_double(mb);
-  const unsigned hi = (unsigned)((unsigned long long)b >> 32);
-  // m as a float: sign, exponent 127, the top 23 significand bits (truncated)
-  const float mf = __uint_as_float((hi & 0x80000000u) | 0x3f800000u | (unsigned)((b >> 29) & 0x7fffff));
-  float rf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(mf));
-  // rf in +-[0.5, 1]: the same value as a double, by moving its fields
-  const unsigned fb = __float_as_uint(rf);
-  const long long rb = ((long long)(fb >> 31) << 63) | ((long long)(((fb >> 23) & 0xff) - 127 + 1023) << 52) |
-                       ((long long)(fb & 0x7fffff) << 29);
-  double r = __longlong_as_double(rb);
-  double e = fma(-m, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-m, r, 1.0);
-  r = fma(r, e, r);
-  // 1/a = r 2^-(ef - 1023); r's exponent field is 1022 or 1023, the result's stays in [1, 2043]
-  return __longlong_as_double(__double_as_longlong(r) - ((long long)(ef - 1023) << 52));
-}
 
 template <>
 __device__ inline double lu_recip<double>(double c) {
@@ -1100,13 +1119,33 @@ __device__ inline FF lu_recip<FF>(double c) {
 
 // Dense LU with partial pivoting (row interchanges, ties to the lowest row), in place, and the
 // substitutions that use it (Sec. 2.3: dense LU + back substitution).  Returns false on an
-// exactly zero pivot.
+// exactly zero pivot.  The factors are stored as P W = L D U': the strictly lower part holds the
+// unit lower factor L, the diagonal the pivots D, invdiag their reciprocals, and the strictly
+// upper part the unit upper factor U' = D^-1 U (each row of U times its pivot's reciprocal, one
+// rounding, after the elimination has used it), so that neither substitution has a multiply in
+// its dependent chain.
 
 // |a| as an ordered integer key (bit pattern of a non-negative float / double)
 // (the sign bit masked off in the integer pipe, so that no FP64 instruction is spent on it)
 __device__ inline long long abs_key(double a) { return __double_as_longlong(a) & 0x7fffffffffffffffLL; }
 __device__ inline long long abs_key(float a) { return (long long)__float_as_int(fabsf(a)); }
 __device__ inline long long abs_key(FF a) { return (long long)__float_as_int(fabsf(a.hi)); }
+
+// U' = D^-1 U: the strictly upper part of row i times invdiag[i], over the N (N - 1) / 2 entries
+// in row order (each thread walks its entries in increasing order and advances its row as it goes).
+template <int G, typename S>
+__device__ inline void lu_unit_upper(const Grp<G>& g, S* A, int N, const S* invdiag) {
+  constexpr int NT = Grp<G>::NT;
+  const int tot = N * (N - 1) / 2;
+  int i = 0, rs = 0;  // the row of the thread's next entry and the index of that row's first entry
+  for (int e = g.t; e < tot; e += NT) {
+    while (e >= rs + N - 1 - i) {
+      rs += N - 1 - i;
+      ++i;
+    }
+    A[i * N + i + 1 + e - rs] *= invdiag[i];
+  }
+}
 
 template <int G, typename S>
 __device__ bool cell_lu(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* invdiag) {
@@ -1182,6 +1221,7 @@ __device__ bool cell_lu(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* in
       perm[p] = t;
     }
   }
+  lu_unit_upper(g, A, N, invdiag);
   g.sync();
   return ok;
 }
@@ -1196,7 +1236,8 @@ __device__ bool cell_lu(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* in
 //   * every thread then combines the G candidates itself (ties to the lowest row) and takes the
 //     pivot's reciprocal, so no thread waits for another to compute it;
 //   * the row interchange (threads over columns) and the scaled multipliers of column k (threads
-//     over rows, reading the interchanged value for the pivot row) form one phase.
+//     over rows, reading the interchanged value for the pivot row) form one phase;
+//   * row k-1 of the unit upper factor is scaled during step k's update (no pass at the end).
 template <int G, typename S>
 __device__ bool cell_lu_fused(const Grp<G>& g, S* A, int N, int* piv, int* perm, S* invdiag) {
   constexpr int NT = Grp<G>::NT;
@@ -1266,6 +1307,11 @@ __device__ bool cell_lu_fused(const Grp<G>& g, S* A, int N, int* piv, int* perm,
       }
     }
     g.sync();
+    // row k-1 of U is final (step k-1's update was its last): U' = D^-1 U there, beside the update
+    if (k > 0) {
+      const S dk = invdiag[k - 1];
+      for (int j = k + g.t; j < N; j += NT) A[(k - 1) * N + j] *= dk;
+    }
     // trailing update: column k+1 first (its entries are the next pivot's candidates, each thread
     // keeping the largest it produced), then the other columns
     const int mm = N - k - 1;
@@ -1463,6 +1509,7 @@ __device__ bool cell_lu_blocked(const Grp<G>& g, S* A, int N, int* piv, int* per
       perm[p] = t;
     }
   }
+  lu_unit_upper(g, A, N, invdiag);
   g.sync();
   return *singular == 0;
 }
@@ -1547,12 +1594,15 @@ __device__ void warp_lu_solve_s(const T* A, int N, const int* perm, const T* inv
       }
     }
   }
-  // back substitution with the upper factor: column j in slot jb updates slots <= jb
+  // D^-1 (all rows at once), then back substitution with the unit upper factor U': column j in
+  // slot jb updates slots <= jb
+#pragma unroll
+  for (int s = 0; s < S; ++s)
+    if (lane + 32 * s < N) xr[s] = xr[s] * invdiag[lane + 32 * s];
 #pragma unroll
   for (int jb = S - 1; jb >= 0; --jb) {
     for (int j = min(32 * jb + 31, N - 1); j >= 32 * jb; --j) {
-      const T xj = shfl(xr[jb], j & 31) * invdiag[j];
-      if (lane == (j & 31)) xr[jb] = xj;
+      const T xj = shfl(xr[jb], j & 31);
 #pragma unroll
       for (int s = 0; s <= jb; ++s) {
         const int i = lane + 32 * s;
@@ -1581,10 +1631,11 @@ __device__ void warp_lu_solve(const double* A, int N, const int* perm, const dou
   warp_lu_solve_any<double>(A, N, perm, invdiag, nullptr, nullptr, x, x);
 }
 
-// x <- W^-T b with the factors of cell_lu (P W = L U, P the row permutation perm): W^T =
-// U^T L^T P, so U^T z = b (forward, column j of U^T is row j of U), L^T w = z (backward, unit
-// diagonal, column j of L^T is row j of L), x[perm[i]] = w[i].  One warp, x in registers as in
-// warp_lu_solve_s; the factor rows are read contiguously.  b and x may alias.
+// x <- W^-T b with the factors of cell_lu (P W = L D U', P the row permutation perm): W^T =
+// U'^T D L^T P, so U'^T v = b (forward, unit diagonal, column j of U'^T is row j of U'),
+// z = D^-1 v, L^T w = z (backward, unit diagonal, column j of L^T is row j of L),
+// x[perm[i]] = w[i].  One warp, x in registers as in warp_lu_solve_s; the factor rows are read
+// contiguously.  b and x may alias.
 template <int S>
 __device__ void warp_lu_solve_t_s(const double* A, int N, const int* perm, const double* invdiag, const double* b,
                                   double* x) {
@@ -1600,16 +1651,18 @@ __device__ void warp_lu_solve_t_s(const double* A, int N, const int* perm, const
   for (int jb = 0; jb < S; ++jb) {
     const int jend = min(32 * jb + 32, N);
     for (int j = 32 * jb; j < jend; ++j) {
-      const double zj = __shfl_sync(kFull, xr[jb], j & 31) * invdiag[j];
-      if (lane == (j & 31)) xr[jb] = zj;
+      const double vj = __shfl_sync(kFull, xr[jb], j & 31);
       const double* Uj = A + (size_t)j * N;
 #pragma unroll
       for (int s = jb; s < S; ++s) {
         const int i = lane + 32 * s;
-        if (i > j && i < N) xr[s] = fma(-Uj[i], zj, xr[s]);
+        if (i > j && i < N) xr[s] = fma(-Uj[i], vj, xr[s]);
       }
     }
   }
+#pragma unroll
+  for (int s = 0; s < S; ++s)
+    if (lane + 32 * s < N) xr[s] *= invdiag[lane + 32 * s];
 #pragma unroll
   for (int jb = S - 1; jb >= 0; --jb) {
     for (int j = min(32 * jb + 31, N - 1); j >= 32 * jb; --j) {

@@ -22,8 +22,8 @@ constexpr int kRxInts = 16;
 //   [0] ln A   [1] b   [2] Ea/Rc (K)   [3..6] net coefficients of the rows (as doubles)
 constexpr int kRxDoubles = 7;
 
-// Per fall-off reaction doubles: ln A0, b0, Ea0/Rc, alpha, T3, T1, T2, is_troe
-constexpr int kFoDoubles = 8;
+// Per fall-off reaction doubles: ln A0, b0, Ea0/Rc, alpha, T3, T1, T2, is_troe, 1/T3, 1/T1
+constexpr int kFoDoubles = 10;
 
 // Per species doubles: W, 1/W, Tmid, NASA low a1..a7, NASA high a1..a7
 constexpr int kSpDoubles = 17;

@@ -284,16 +284,20 @@ int set_err(int code, const std::string& msg) {
 
 // Reaction split of cell_rates for a group of G warps.  The fall-off reactions come first in
 // device order (Troe, then Lindemann), and a warp iteration that holds a Troe reaction costs about
-// six plain ones (measured with clock64() per warp on the 53-species mechanism: 39 k against
-// 6.1 k cycles; three more exponentials, two logarithms and five quotients), so interleaving the
+// five plain ones (measured with clock64() per warp on the 53-species mechanism, evaluation with
+// the Jacobian data: 34.7 k against 7.2 k cycles; four more exponentials, two logarithms and
+// four Newton reciprocals), so interleaving the
 // reactions over all warps leaves warp 0 with the slowest iterations while the others wait at the
 // next barrier.  Warp 0 takes reactions [0, a) and the other G - 1 warps [a, R), with a a multiple
 // of 32, at least the fall-off count, that minimises the larger side's cost (a warp iteration
-// costing 6 with a Troe reaction, 2 with a Lindemann one, else 1).  If the plain interleaving
+// costing 5 with a Troe reaction, 2 with a Lindemann one, else 1).  If the plain interleaving
 // (reaction r to thread r mod 32 G) costs no more, the split is 0, which keeps it.
+#ifndef CHEM_TROE_ITER_COST
+#define CHEM_TROE_ITER_COST 5
+#endif
 int reaction_split(int R, int n_troe, int n_fo, int G) {
   if (G <= 1) return R;
-  auto iter_cost = [&](int s) { return (s < n_troe) ? 6 : (s < n_fo) ? 2 : 1; };
+  auto iter_cost = [&](int s) { return (s < n_troe) ? CHEM_TROE_ITER_COST : (s < n_fo) ? 2 : 1; };
   int inter = 0;
   for (int w = 0; w < G; ++w) {
     int c = 0;

@@ -93,7 +93,7 @@ __device__ inline FF to_low<FF>(double v) { return FF(v); }
 // buffer B; the reciprocal pivots go to invd.  The diagonal gh + (-J)_ii is formed once in FP64
 // (in the residual vector, free until the stage solves), so the scans only compare exponents.
 template <int G, typename L>
-__device__ bool form_and_factor_low(const Grp<G>& g, const CellMem& w, int N, double gh, L* invd) {
+__device__ __forceinline__ bool form_and_factor_low(const Grp<G>& g, const CellMem& w, int N, double gh, L* invd) {
   constexpr int NT = Grp<G>::NT;
   L* S = reinterpret_cast<L*>(w.B);
   double* dg = w.res;
@@ -139,7 +139,7 @@ __device__ inline const FF* invd_of(const CellMem& w, FF*) { return reinterpret_
 // as an FP64 solve can be checked to be).  Returns false if neither happens.  FP32 pairs with
 // refine_sweeps = 0 take the first solve as it is.
 template <int G, typename L>
-__device__ bool stage_solve_low(const Grp<G>& g, const CellMem& w, const IntegrateArgs& a, int N, double gh,
+__device__ __forceinline__ bool stage_solve_low(const Grp<G>& g, const CellMem& w, const IntegrateArgs& a, int N, double gh,
                                 double* u) {
   constexpr int NT = Grp<G>::NT;
   const L* invd = invd_of(w, (L*)nullptr);
@@ -188,7 +188,7 @@ __device__ bool stage_solve_low(const Grp<G>& g, const CellMem& w, const Integra
 
 // u <- W^-1 rhs: FP64 factors (lowp 0: one solve), FP32 factors (1) or FP32 pairs (2).
 template <int G>
-__device__ bool stage_solve(const Grp<G>& g, const CellMem& w, const IntegrateArgs& a, int N, double gh, int lowp,
+__device__ __forceinline__ bool stage_solve(const Grp<G>& g, const CellMem& w, const IntegrateArgs& a, int N, double gh, int lowp,
                             double* u) {
   constexpr int NT = Grp<G>::NT;
   if (lowp == 1) return stage_solve_low<G, float>(g, w, a, N, gh, u);

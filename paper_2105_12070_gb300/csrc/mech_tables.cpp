@@ -305,6 +305,8 @@ bool build_tables(const char* path, HostMech& m, std::vector<FileReaction>& rx, 
       q[0] = std::log(x.A0); q[1] = x.b0; q[2] = x.Ea0 / kRcal;
       q[3] = x.troe[0]; q[4] = x.troe[1]; q[5] = x.troe[2]; q[6] = x.troe[3];
       q[7] = (x.type == kTroe) ? 1.0 : 0.0;
+      q[8] = (x.type == kTroe) ? 1.0 / x.troe[1] : 0.0;
+      q[9] = (x.type == kTroe) ? 1.0 / x.troe[2] : 0.0;
     }
   }
   m.sr_ptr.assign(K + 1, 0);

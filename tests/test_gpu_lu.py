@@ -3,6 +3,8 @@ chem_debug_lu: its schedule with two barriers per column (the integrate kernels'
 panel-blocked schedule give bitwise the factors of the column-by-column one in every factor
 precision (the same pivots and the same operations on every entry, in the same order), and the FP64 factors equal LAPACK's (scipy.linalg.lu_factor, whose pivot is also the
 first largest |a|) on random matrices, with reciprocal pivots within one unit in the last place.
+The factors are stored as P A = L D U' (U' = D^-1 U, unit upper): the upper factor is rebuilt
+from them as U = D U' for the comparison.
 """
 import numpy as np
 import pytest
@@ -54,7 +56,10 @@ def test_fp64_lu_matches_lapack(N):
         for k, p in enumerate(piv):
             perm[[k, p]] = perm[[p, k]]
         np.testing.assert_array_equal(P[m], perm)
-        f = F[m].reshape(N, N)
+        f = F[m].reshape(N, N).copy()
+        # U = D U': the strictly upper part row by row times the pivot on the diagonal
+        up = np.triu(np.ones((N, N), dtype=bool), 1)
+        f[up] = (f * np.diag(f)[:, None])[up]
         scale = np.abs(lu).max(axis=1, keepdims=True)
         assert np.all(np.abs(f - lu) <= 1e-10 * scale), m
         # the reciprocal pivots (Newton's iteration): within one unit in the last place of 1 / u_kk
