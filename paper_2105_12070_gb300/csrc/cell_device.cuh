@@ -1080,6 +1080,21 @@ __device__ inline FF fma(FF a, FF b, FF c) {
   e = __fadd_rn(e, __fadd_rn(c.lo, pe));
   return ff_norm(s, e);
 }
+// a b + c for the running sums of the substitutions: the same terms as fma, without the final
+// renormalisation, so the pair (s, e) has s + e = c.hi + fl(a.hi b.hi) exactly and the product's
+// error and c.lo summed into e (|e| grows with the rounding errors of the sum, about the same
+// error as renormalising every step; the pair is only renormalised where it is converted)
+__device__ inline FF fma_acc(FF a, FF b, FF c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float pe = fmaf(a.hi, b.hi, -p);
+  pe = fmaf(a.hi, b.lo, pe);
+  pe = fmaf(a.lo, b.hi, pe);
+  float s, e;
+  two_sum(c.hi, p, s, e);
+  return FF(s, __fadd_rn(e, __fadd_rn(c.lo, pe)));
+}
+__device__ inline double fma_acc(double a, double b, double c) { return fma(a, b, c); }
+__device__ inline float fma_acc(float a, float b, float c) { return fmaf(a, b, c); }
 // 1 / a: the FP32 reciprocal of hi and one Newton correction r (1 - a r) in pair arithmetic
 __device__ inline FF ff_recip(FF a) {
   const float r = 1.0f / a.hi;
@@ -1565,6 +1580,28 @@ __device__ inline double high_of(double v) { return v; }
 __device__ inline double high_of(float v) { return f64_of(v); }
 __device__ inline double high_of(FF v) { return (double)v; }
 
+// One column step of the register substitutions of warp_lu_solve_s: broadcast x_j from its lane,
+// then one FMA per slot holding a row below (forward, unit lower factor) or above (backward, unit
+// upper factor) the column.
+template <int S, typename T>
+__device__ __forceinline__ void fwd_column(T (&xr)[S], const T* A, int N, int lane, int jb, int j) {
+  const T xj = shfl(xr[jb], j & 31);
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int i = lane + 32 * s;
+    if (s >= jb && i > j && i < N) xr[s] = fma_acc(-A[i * N + j], xj, xr[s]);
+  }
+}
+template <int S, typename T>
+__device__ __forceinline__ void bwd_column(T (&xr)[S], const T* A, int N, int lane, int jb, int j) {
+  const T xj = shfl(xr[jb], j & 31);
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int i = lane + 32 * s;
+    if (s <= jb && i < j) xr[s] = fma_acc(-A[i * N + j], xj, xr[s]);
+  }
+}
+
 template <int S, typename T>
 __device__ void warp_lu_solve_s(const T* A, int N, const int* perm, const T* invdiag, const int* er, const int* ec,
                                 const double* b, double* x) {
@@ -1581,17 +1618,18 @@ __device__ void warp_lu_solve_s(const T* A, int N, const int* perm, const T* inv
     xr[s] = v;
   }
   __syncwarp();
-  // forward substitution with the unit lower factor: column j in slot jb updates slots >= jb
+  // forward substitution with the unit lower factor: column j in slot jb updates slots >= jb.
+  // FP32 and pair columns are unrolled four deep (their short chains leave instruction issue as
+  // the cost: -11 % and -12 % solve time); FP64 columns keep the compiler's own loop (its chain is
+  // the FP64 latency, and forcing an unroll factor made it 5-7 % slower)
 #pragma unroll
   for (int jb = 0; jb < S; ++jb) {
     const int jend = min(32 * jb + 32, N - 1);
-    for (int j = 32 * jb; j < jend; ++j) {
-      const T xj = shfl(xr[jb], j & 31);
-#pragma unroll
-      for (int s = jb; s < S; ++s) {
-        const int i = lane + 32 * s;
-        if (i > j && i < N) xr[s] = fma(-A[i * N + j], xj, xr[s]);
-      }
+    if (std::is_same<T, double>::value) {
+      for (int j = 32 * jb; j < jend; ++j) fwd_column<S>(xr, A, N, lane, jb, j);
+    } else {
+#pragma unroll 4
+      for (int j = 32 * jb; j < jend; ++j) fwd_column<S>(xr, A, N, lane, jb, j);
     }
   }
   // D^-1 (all rows at once), then back substitution with the unit upper factor U': column j in
@@ -1601,13 +1639,11 @@ __device__ void warp_lu_solve_s(const T* A, int N, const int* perm, const T* inv
     if (lane + 32 * s < N) xr[s] = xr[s] * invdiag[lane + 32 * s];
 #pragma unroll
   for (int jb = S - 1; jb >= 0; --jb) {
-    for (int j = min(32 * jb + 31, N - 1); j >= 32 * jb; --j) {
-      const T xj = shfl(xr[jb], j & 31);
-#pragma unroll
-      for (int s = 0; s <= jb; ++s) {
-        const int i = lane + 32 * s;
-        if (i < j) xr[s] = fma(-A[i * N + j], xj, xr[s]);
-      }
+    if (std::is_same<T, double>::value) {
+      for (int j = min(32 * jb + 31, N - 1); j >= 32 * jb; --j) bwd_column<S>(xr, A, N, lane, jb, j);
+    } else {
+#pragma unroll 4
+      for (int j = min(32 * jb + 31, N - 1); j >= 32 * jb; --j) bwd_column<S>(xr, A, N, lane, jb, j);
     }
   }
 #pragma unroll
