@@ -55,12 +55,12 @@ FLOP_WEIGHTS = {"add": 1, "mul": 1, "div": 1, "exp": 2 * 17, "log": 2 * 31}
 # DRAM bytes (read + write) of the integrate kernel as a function of the cells of a launch,
 # fitted to two ncu captures (dram__bytes_read.sum + dram__bytes_write.sum, the timed launch of
 # `bench.py --cells n --dt 1e-9 --warmup 1 --steps 1`) of the current kernel on evenly spaced
-# slices of the shear-layer field: 1 342 464 B read / 0 B written at 608 cells and 3 317 760 B /
+# slices of the shear-layer field: 1 566 720 B read / 0 B written at 608 cells and 3 371 264 B /
 # 0 B at 4864 cells, i.e. fixed bytes (mechanism tables, the CTAs' first touches) plus bytes per
 # cell (its state; the rest of the state is read from L2, where the library's staging copy in
 # the same call left it, and the results stay in L2 until the copy back).
-TRAFFIC_FIT = {"fixed": 1342464 - 608 * (3317760 - 1342464) / (4864 - 608),
-               "per_cell": (3317760 - 1342464) / (4864 - 608), "cells": (608, 4864)}
+TRAFFIC_FIT = {"fixed": 1566720 - 608 * (3371264 - 1566720) / (4864 - 608),
+               "per_cell": (3371264 - 1566720) / (4864 - 608), "cells": (608, 4864)}
 
 
 def parse_args(argv=None):
