@@ -289,6 +289,17 @@ class Budget:
             return True  # at least one timed step
         return self.elapsed(now) + step_s + reserve_s <= self.limit
 
+    def projection(self, done: int, requested: int, step_s: float, reserve_s: float, now=None) -> dict:
+        """The steps that fit at the measured step time (all requested ones, or fewer) and the
+        projected end of the run, for the log line after the first timed step."""
+        t = self.elapsed(now)
+        n = done
+        while n < requested and t + step_s + reserve_s <= self.limit:
+            t += step_s
+            n += 1
+        return {"steps_that_fit": n, "requested": requested, "projected_end_s": t + reserve_s,
+                "limit_s": self.limit}
+
 
 def workload_config(w, precision, refine_sweeps, solver, **extra):
     K = w["mech"].K
@@ -681,6 +692,11 @@ def run_forward(args, w, world, rank, local):
         kern_ms += k
         wall_ms += wms
         done += 1
+        if done == 1 and rank == 0:
+            pj = budget.projection(done, args.steps, wms / 1e3, reserve)
+            print(f"bench: first timed step {wms / 1e3:.1f} s; {pj['steps_that_fit']} of {pj['requested']} steps "
+                  f"fit, projected end {pj['projected_end_s']:.0f} s of the {pj['limit_s']:.0f} s budget",
+                  file=sys.stderr, flush=True)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()

@@ -95,6 +95,22 @@ def test_budget_guard(bench):
     assert not b.may_continue(5, 5, 0.0, 0.0, now=0.0)  # all requested steps done
 
 
+def test_budget_projection(bench):
+    """The driver's run: 20 steps of 83.3 s after ~25 s of start-up and CPU legs fit in 1740 s
+    with the 20 s reserve; at 85.2 s per step only 19 do."""
+    b = bench.Budget(1740.0, t0=0.0)
+    pj = b.projection(1, 20, 83.3, 20.0, now=25.0 + 83.3)
+    assert pj["steps_that_fit"] == 20 and pj["projected_end_s"] <= 1740.0
+    assert b.projection(1, 20, 85.2, 20.0, now=25.0 + 85.2)["steps_that_fit"] == 19
+    # the projection agrees with the loop's own test step by step
+    done, now = 1, 25.0 + 85.2
+    while b.may_continue(done, 20, 85.2, 20.0, now=now):
+        done += 1
+        now += 85.2
+    assert done == 19
+    assert bench.parse_args([]).budget_s == 1740.0
+
+
 def test_sample_sizes(bench):
     n_all, n_one = bench.sample_sizes(36.0, 16, 15.0, 65536)
     assert n_all % 16 == 0 and 16 <= n_all <= 65536 and abs(n_all / 36.0 - 15.0) < 1.0
