@@ -616,9 +616,9 @@ def run_forward(args, w, world, rank, local):
         idx = np.arange(n_total) % n_field
         w = dict(w, T=w["T"][idx].copy(), Y=w["Y"][:, idx].copy(), name=f"{w['name']}_tiled{n_total}")
     # the CPU oracle's legs first, on the host cores while the GPU is idle, so that the budget of
-    # the timed loop needs no reserve for them
+    # the timed loop needs no reserve for them (one process only: N = 1)
     cb = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w, args.cpu_seconds)
         cb.pop("seconds", None)
     T_host = torch.from_numpy(w["T"].copy()).pin_memory()
